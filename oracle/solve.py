@@ -1,0 +1,140 @@
+"""Oracle: linear solves of the constrained system.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The paper factorises the global matrix once with SuperLU and then solves one
+right-hand side per probe position (Sec. 3, Steps 5-6).  The oracle offers:
+  * dense_solve    numpy.linalg.solve (LAPACK LU) for tiny meshes;
+  * superlu_solve  scipy's SuperLU, the paper's own solver family;
+  * block_jacobi   the inverses of the diagonal blocks of the scaled matrix
+                   over the node subdomains (the subdomain-block
+                   preconditioner: z = blockdiag(S_ss)^-1 r);
+  * fgmres         restarted flexible GMRES (Saad's algorithm) with
+                   classical Gram-Schmidt applied twice, complex Givens
+                   rotations for the Hessenberg least-squares problem, and a
+                   right preconditioner (plain GMRES when it is None).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def dense_solve(M, b):
+    return np.linalg.solve(M.toarray() if sp.issparse(M) else M, b)
+
+
+def superlu_solve(M, b):
+    lu = spla.splu(sp.csc_matrix(M))
+    return lu.solve(np.asarray(b)), lu
+
+
+def block_ranges(block_of_node):
+    """Dof ranges [start, stop) of each subdomain block (4 dofs per node)."""
+    bon = np.asarray(block_of_node)
+    starts = np.flatnonzero(np.r_[True, bon[1:] != bon[:-1]])
+    stops = np.r_[starts[1:], bon.size]
+    return 4 * starts, 4 * stops
+
+
+def block_jacobi(S, block_of_node):
+    """Dense inverses of the diagonal blocks S[s:e, s:e]."""
+    S = sp.csr_matrix(S)
+    starts, stops = block_ranges(block_of_node)
+    inv = []
+    for s, e in zip(starts, stops):
+        inv.append(np.linalg.inv(S[s:e, s:e].toarray()))
+    return starts, stops, inv
+
+
+def block_jacobi_apply(P, r):
+    starts, stops, inv = P
+    z = np.empty_like(r, dtype=np.complex128)
+    for s, e, B in zip(starts, stops, inv):
+        z[s:e] = B @ r[s:e]
+    return z
+
+
+def givens(a, b):
+    """Complex Givens rotation (c real, s complex) with [c s; -conj(s) c][a; b] = [r; 0]."""
+    if b == 0.0:
+        return 1.0, 0.0 + 0.0j, a
+    if a == 0.0:
+        return 0.0, 1.0 + 0.0j, b
+    rho = np.sqrt(abs(a) ** 2 + abs(b) ** 2)
+    ph = a / abs(a)
+    return abs(a) / rho, ph * np.conj(b) / rho, ph * rho
+
+
+def cgs2(V, w):
+    """Orthogonalise w against the orthonormal columns of V twice (CGS2).
+
+    Returns (h, w_new, beta) with h = coefficients accumulated over both
+    passes (Hermitian inner product) and beta = ||w_new||."""
+    h1 = V.conj().T @ w
+    w = w - V @ h1
+    h2 = V.conj().T @ w
+    w = w - V @ h2
+    return h1 + h2, w, np.linalg.norm(w)
+
+
+def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000):
+    """Restarted right-preconditioned flexible GMRES.
+
+    A and precond are callables (or matrices).  Stops when the true residual
+    ||b - A x|| / ||b|| <= tol at a restart, or after maxiter iterations.
+    Returns (x, info) with info = dict(iters, relres, history)."""
+    mv = A if callable(A) else (lambda v: A @ v)
+    pc = (lambda v: v) if precond is None else (precond if callable(precond) else (lambda v: precond @ v))
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    hist = []
+    if bnorm == 0.0:
+        return np.zeros(n, dtype=np.complex128), dict(iters=0, relres=0.0, history=hist)
+    total = 0
+    r = b - mv(x)
+    beta = np.linalg.norm(r)
+    while True:
+        relres = beta / bnorm
+        hist.append(relres)
+        if relres <= tol or total >= maxiter:
+            break
+        m = min(restart, maxiter - total)
+        V = np.zeros((n, m + 1), dtype=np.complex128)
+        Z = np.zeros((n, m), dtype=np.complex128)
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        cs = np.zeros(m)
+        sn = np.zeros(m, dtype=np.complex128)
+        g = np.zeros(m + 1, dtype=np.complex128)
+        g[0] = beta
+        V[:, 0] = r / beta
+        k = 0
+        for j in range(m):
+            Z[:, j] = pc(V[:, j])
+            w = mv(Z[:, j])
+            h, w, hn = cgs2(V[:, :j + 1], w)
+            H[:j + 1, j] = h
+            H[j + 1, j] = hn
+            for i in range(j):                      # previous rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            c, s, rr = givens(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = c, s
+            H[j, j] = rr
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(s) * g[j]
+            g[j] = c * g[j]
+            k = j + 1
+            total += 1
+            if hn == 0.0 or abs(g[j + 1]) / bnorm <= tol:
+                break
+            V[:, j + 1] = w / hn
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + Z[:, :k] @ y
+        r = b - mv(x)
+        beta = np.linalg.norm(r)
+    return x, dict(iters=total, relres=beta / bnorm, history=hist)

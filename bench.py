@@ -1,0 +1,402 @@
+"""Probe solves/s of the eddy-current FE solver on the 4M-DOF tube + support-plate workload.
+
+Workload (config 2 of the benchmark table): 53 x 53 x 356-node jittered Kuhn
+tetrahedral mesh (1,000,004 nodes, 4,000,016 complex unknowns, 5,759,520 tets)
+of a 30 x 30 x 200 mm box around a tube (sigma 1e6) through a quatrefoil
+support plate (sigma 1.4e6, the defect configuration) at 100 kHz; the probe's
+coil pair sits at the plate edge.  One probe position = 4 solves (2 coils x
+{vacuum, defect}) + Delta Z.  Inputs are synthetic and seeded (ect_inputs).
+
+A step is one batch of probe positions through the whole hot path: coil
+sources, batched solves of both systems, Delta Z.  Assembly and the
+preconditioner set-up are done once before timing (the matrix does not
+depend on the probe position) and reported separately.
+
+  value       solves/s with the sources already in HBM (ect_solve on device
+              buffers + the Delta Z reduction), mixed FP32/FP64 + batched
+  e2e         the same metric through ect_impedance with host buffers (host
+              positions in, host Delta Z out, copies inside the timed region)
+  fp64_plain  solves/s of the plain FP64 flexible GMRES, one position
+  roofline    the dominant kernel (FP32 SpMM inside the mixed solve), timed
+              with CUDA events on the library stream
+
+--impl reference times the CPU oracle (the reference for this workload) on a
+bounded sample of the same workload on the host cores.
+Multi-GPU: positions are sharded across ranks (no collective on the data
+path); value = all ranks' solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def probe_positions(n, rank=0, world=1):
+    """Positions around the plate edge (z = 10 mm), 0.5 mm apart, sharded by rank."""
+    z = 10.0e-3 + 0.5e-3 * (np.arange(n * world) - (n * world) // 2)
+    return z[rank * n:(rank + 1) * n]
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import ect_inputs as E
+    from paper_1602_03207_gb300 import build as B
+    from paper_1602_03207_gb300 import ect
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    ect.load_library()
+
+    t0 = time.time()
+    p = E.make_config(args.config)
+    m = p.mesh
+    gen_s = time.time() - t0
+    ctx = ect.Context()
+    ctx.load_problem(p)
+    n = 4 * m.n_nodes
+    mask = ect.ECT_F64 | ect.ECT_F32
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    asm_ms = [timed(lambda w=w: ctx.assemble(w, mask)) for w in (0, 1)]
+    pc_ms = [timed(lambda w=w: ctx.precond_setup(w, mask)) for w in (0, 1)]
+    _, nnzb = ctx.matrix_info()
+
+    P = args.positions
+    zs = probe_positions(P, rank, world)
+    cur = [c.current for c in p.coils]
+    mixed = ect.default_options(tol=args.tol, mode=ect.ECT_MODE_MIXED, restart=args.outer_restart,
+                                inner_iters=args.inner_iters, max_iters=args.max_outer, use_graph=1)
+    plain = ect.default_options(tol=args.tol, mode=ect.ECT_MODE_F64, restart=args.restart, use_graph=1,
+                                max_iters=args.max_iters)
+    # device-resident sources: [P][2][n] (position-major, coil minor)
+    Bsrc = torch.empty(P, 2, n, dtype=torch.complex128, device="cuda")
+    for c in range(2):
+        tmp = torch.empty(P, n, dtype=torch.complex128, device="cuda")
+        ctx.coil_rhs(p.coils[c], zs, tmp)
+        Bsrc[:, c] = tmp
+    del tmp
+    U0 = torch.empty_like(Bsrc)
+    Ud = torch.empty_like(Bsrc)
+    k = 2 * P
+
+    stats = {}
+
+    def step_device(opts, tag):
+        s0 = ctx.solve(0, Bsrc, U0, k, opts)
+        s1 = ctx.solve(1, Bsrc, Ud, k, opts)
+        for q in range(P):
+            ctx.delta_z(U0[q], Ud[q], None, cur)
+        stats[tag] = (s0, s1)
+
+    for _ in range(args.warmup):
+        step_device(mixed, "mixed")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step_device(mixed, "mixed")
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        dist.barrier()
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    solves = 4 * P * world * args.steps
+    value = solves / (ms / 1000.0)
+
+    # e2e: the public host-buffer call (host positions in, host Delta Z out)
+    for _ in range(1):
+        ctx.impedance(p.coils, zs, mixed)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    dz_e2e = None
+    for _ in range(args.steps):
+        dz_e2e, _ = ctx.impedance(p.coils, zs, mixed)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t1
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = 4 * P * world * args.steps / e2e_s
+
+    # plain FP64, one position (4 solves)
+    plain_ms = None
+    dz_plain = None
+    if not args.skip_plain:
+        z1 = zs[:1]
+        dz_plain, _ = ctx.impedance(p.coils, z1, plain)      # warm-up (captures graphs)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        dz_plain, sp = ctx.impedance(p.coils, z1, plain)
+        torch.cuda.synchronize()
+        plain_ms = (time.perf_counter() - t2) * 1000.0
+        stats["plain"] = sp
+    # Delta Z of mixed vs plain FP64 at the shared position
+    dz_err = None
+    if dz_plain is not None and dz_e2e is not None:
+        dz_err = float(np.abs(dz_e2e[0] - dz_plain[0]).max() / np.abs(dz_plain[0]).max())
+
+    # dominant kernel: FP32 SpMM at the solver's tile (8 rhs per matrix pass)
+    kk = min(k, 8)
+    xs = torch.randn(kk, n, dtype=torch.complex64, device="cuda")
+    ys = torch.empty_like(xs)
+    for _ in range(3):
+        ctx.spmv(0, xs, ys, kk, precision=ect.ECT_F32)
+    reps = 20
+    ctx_stream = torch.cuda.ExternalStream(ctx.stream.cuda_stream)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(ctx_stream)
+    for _ in range(reps):
+        ctx.spmv(0, xs, ys, kk, precision=ect.ECT_F32)
+    a1.record(ctx_stream)
+    torch.cuda.synchronize()
+    spmv_ms = a0.elapsed_time(a1) / reps
+    nrows = m.n_nodes
+    spmv_bytes = nnzb * (16 * 8 + 4) + 4 * (nrows + 1) + 2 * kk * n * 8
+    achieved = spmv_bytes / (spmv_ms / 1000.0) / 1e9
+    peaks, src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+
+    rec = {
+        "metric": "probe solves/s at 4M complex DOF, FP64 plain vs mixed+batched, dZ err<=1e-6",
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64/c128 (mixed FP32 inner, FP64 outer)",
+        "data": "synthetic (seeded jittered Kuhn mesh, ect_inputs)",
+        "config": {"workload": f"{args.config}: {m.n_nodes} nodes / {n} complex dof / {m.n_tets} tets, "
+                               f"{P} probe positions per rank per step (= {4 * P} solves), tol {args.tol}",
+                   "positions_per_step": P * world, "rhs_per_solve_call": k, "nnzb": nnzb,
+                   "inner_iters": args.inner_iters, "outer_restart": args.outer_restart,
+                   "l2": "inputs larger than L2 (matrices 3.8 GB FP64 / 1.9 GB FP32 each)",
+                   "parallelism": f"positions sharded over {world} GPU(s)"},
+        "clocks": clocks,
+        "e2e": {"value": e2e, "unit": "solves/s", "h2d_bytes_per_step": 8 * P + 2 * 40,
+                "d2h_bytes_per_step": 64 * P},
+        "fp64_plain": {"value": (4.0 / (plain_ms / 1000.0)) if plain_ms else None, "unit": "solves/s",
+                       "ms_per_position": plain_ms,
+                       "stats": stats.get("plain")},
+        "dz_rel_err_mixed_vs_fp64": dz_err,
+        "solver_stats": {"mixed_vacuum": stats["mixed"][0], "mixed_defect": stats["mixed"][1]},
+        "setup_ms": {"mesh_gen_s": gen_s * 1000, "assemble": asm_ms, "precond": pc_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": f"k_spmv_f32<8> (SpMM, {kk} rhs)", "ms_per_launch": spmv_ms,
+                     "algorithmic_bytes": spmv_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
+        "gpu_launches": None,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline(args, stats)
+    if rank == 0:
+        print(json.dumps(rec))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(args, budget_s=20.0, iters_per_solve=None):
+    """Time the oracle's block-Jacobi FGMRES on a slab of the same workload.
+
+    The slab keeps the full 53 x 53 cross-section and 40 node layers of the
+    z-range around the plate edge (same h, materials, jitter recipe);
+    seconds per iteration per unknown are measured and scaled to the full
+    4,000,016 unknowns and to the iterations one solve needs."""
+    import ect_inputs as E
+    from oracle import fem, rhs, solve
+
+    shape, lengths, jitter = E.CONFIGS[args.config]
+    nz = 40
+    Lz = lengths[2] * (nz - 1) / (shape[2] - 1)
+    p = E.tsp_problem((shape[0], shape[1], nz), (lengths[0], lengths[1], Lz), jitter=jitter, z_pos=(0.0,))
+    t0 = time.time()
+    M = fem.system_matrix(p, "defect")
+    asm_s = time.time() - t0
+    t = fem.scaling(M)
+    S = fem.scaled(M, t)
+    P = solve.block_jacobi(S, p.mesh.block_of_node)
+    b = fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, p.coils[0].as_tuple(), 0.0), p, "defect")
+    it = 0
+    t1 = time.time()
+    x = None
+    while time.time() - t1 < budget_s:
+        x, info = solve.fgmres(S, t * b, lambda r: solve.block_jacobi_apply(P, r), tol=1e-30, restart=30,
+                               maxiter=30, x0=x)
+        it += info["iters"]
+    el = time.time() - t1
+    n_small = 4 * p.mesh.n_nodes
+    n_full = 4 * shape[0] * shape[1] * shape[2]
+    s_per_iter_dof = el / it / n_small
+    ips = iters_per_solve or 1000
+    solves_per_s = 1.0 / (s_per_iter_dof * n_full * ips)
+    return {"value": solves_per_s, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle FGMRES(30)+block-Jacobi on a {shape[0]}x{shape[1]}x{nz}-node slab of the "
+                       f"workload ({n_small} dof): {it} iterations in {el:.1f} s, scaled to {n_full} dof and "
+                       f"{ips} iterations/solve (the GPU FP64 run's count); slab assembly {asm_s:.1f} s")}
+
+
+def cpu_baseline(args, stats):
+    ips = None
+    if stats.get("plain"):
+        ips = stats["plain"].get("iters") or None
+    return oracle_sample(args, budget_s=args.cpu_budget, iters_per_solve=ips)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    t0 = time.time()
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(oracle_sample(args, budget_s=args.ref_budget, iters_per_solve=args.ref_iters))
+    v = vals[-args.steps:]
+    value = statistics.median([x["value"] for x in v])
+    rec = {"impl": "reference", "metric": "probe solves/s at 4M complex DOF, FP64 plain vs mixed+batched, "
+           "dZ err<=1e-6", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded, ect_inputs)",
+           "config": {"workload": f"{args.config} (oracle sample)"},
+           "cpu_baseline": dict(v[-1], value=value),
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": time.time() - t0}
+    print(json.dumps(rec))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--positions", type=int, default=4)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--outer-restart", type=int, default=10)
+    ap.add_argument("--max-outer", type=int, default=400)
+    ap.add_argument("--inner-iters", type=int, default=30)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--ref-iters", type=int, default=1000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * ect.h - C ABI of the GB300 eddy-current finite-element solver.
+ *
+ * The library assembles and solves the discrete time-harmonic eddy-current
+ * problem in the Coulomb-gauged A-V potential formulation with P1 nodal
+ * elements on tetrahedra (Riahi, "A Fast Eddy-current Non Destructive Testing
+ * Finite Element Solver in Steam Generator", Sec. 2-3), and reads out the
+ * coil-impedance change Delta Z of Eq. impedkl for each probe position.
+ *
+ * Conventions for every entry point
+ *   - Return value: ECT_OK (0) or one of the ECT_ERR_* codes below; on error
+ *     ect_last_error() describes it.  No C++ exception crosses the ABI.
+ *   - Pointers prefixed h_ are host memory, d_ device memory (any allocator,
+ *     e.g. torch tensors).  Host inputs are copied; the caller keeps
+ *     ownership of every buffer it passes.
+ *   - Complex values are interleaved (re, im) pairs: double[2] for complex128,
+ *     float[2] for complex64.
+ *   - Unknowns are ordered per node as (A_x, A_y, A_z, V); a vector of one
+ *     right-hand side has 4*n_nodes complex entries, dof = 4*node + comp.
+ *     A batch of k vectors is stored [k][n_nodes][4] (each vector contiguous).
+ *   - All GPU work is enqueued on the stream given to ect_create; calls that
+ *     return host data synchronise that stream.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef ECT_H
+#define ECT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define ECT_OK 0
+#define ECT_ERR_ARG 1            /* invalid argument (null, size, range)       */
+#define ECT_ERR_MESH 2           /* bad mesh: index out of range, volume <= 0  */
+#define ECT_ERR_CUDA 3           /* a CUDA call failed                          */
+#define ECT_ERR_OOM 4            /* device allocation failed                    */
+#define ECT_ERR_NOT_CONVERGED 5  /* tolerance not met; x and stats are filled   */
+#define ECT_ERR_BREAKDOWN 6      /* NaN/Inf in the Krylov recurrence            */
+#define ECT_ERR_TIMEOUT 7        /* options.timeout_s expired; x is filled      */
+#define ECT_ERR_STATE 8          /* call out of order (e.g. solve before assemble) */
+
+/* ---- which matrix ---------------------------------------------------------- */
+#define ECT_VACUUM 0             /* background configuration ("vacuum", Sec. 2 remark) */
+#define ECT_DEFECT 1             /* configuration with the defect region Omega_d       */
+
+/* ---- precision ------------------------------------------------------------- */
+#define ECT_F64 1                /* complex128 */
+#define ECT_F32 2                /* complex64  */
+
+/* solver modes (ect_options.mode) */
+#define ECT_MODE_F64 0           /* flexible GMRES, everything in FP64                   */
+#define ECT_MODE_MIXED 1         /* FP64 flexible GMRES outer loop, FP32 GMRES inner solve */
+
+typedef struct ect_ctx ect_ctx;
+
+/* Annular coil with azimuthal current density J_e (Sec. 4): it occupies
+ * r_in <= r <= r_out around the z axis and |z - (z_probe + z_offset)| <= length/2.
+ * Lengths in metres, J_e in A/m^2. */
+typedef struct {
+    double r_in, r_out, length, z_offset, J_e;
+} ect_coil;
+
+typedef struct {
+    double tol;         /* relative residual ||T(b - M x)|| / ||T b|| (T = diag |M_ii|^-1/2) */
+    int restart;        /* Krylov restart length m (outer length in mixed mode)           */
+    int max_iters;      /* cap on outer iterations (F64: all iterations)                  */
+    int mode;           /* ECT_MODE_F64 or ECT_MODE_MIXED                                 */
+    int inner_iters;    /* mixed mode: FP32 GMRES iterations per outer step               */
+    int use_graph;      /* 1: replay each restart cycle as a captured CUDA graph           */
+    int rhs_tile;       /* right-hand sides per SpMM/preconditioner pass (0 = auto)        */
+    double timeout_s;   /* wall-clock limit of one solve call (0 = none)                  */
+} ect_options;
+
+typedef struct {
+    int iters;          /* Krylov iterations (inner ones in mixed mode), max over rhs */
+    int outer_iters;    /* outer iterations, max over rhs                             */
+    int converged;      /* number of right-hand sides that met tol                    */
+    int restarts;       /* restart cycles run                                          */
+    double relres_max;  /* max over rhs of the true relative residual at exit          */
+    double ms;          /* device time of the call (CUDA events on the context stream) */
+} ect_stats;
+
+/* Fill *opt with defaults: tol 1e-10, restart 30, max_iters 20000, F64 mode,
+ * inner_iters 30, graphs on, automatic rhs tile, no timeout. */
+void ect_default_options(ect_options* opt);
+
+/* Create a context bound to a CUDA stream (a cudaStream_t, may be NULL for the
+ * legacy default stream) on the current device.  Free with ect_destroy. */
+int ect_create(ect_ctx** out, void* cuda_stream);
+void ect_destroy(ect_ctx* ctx);
+
+/* Message of the last error on this context (or of the last failed
+ * ect_create on this thread when ctx is NULL).  Never NULL. */
+const char* ect_last_error(const ect_ctx* ctx);
+
+/* Step 1-2 of Sec. 3: the triangulation and its partition.
+ *   h_xyz            double[n_nodes][3] node coordinates (metres)
+ *   h_tets           int32[n_tets][4] node indices, positively oriented
+ *   h_sigma, h_nu    double[n_tets] background conductivity and 1/mu
+ *   h_sigma_d, h_nu_d double[n_tets] defect configuration; NaN = same as background
+ *                    (both may be NULL: no defect)
+ *   h_block_of_node  int32[n_nodes] subdomain id of each node; must be
+ *                    non-decreasing from 0 in steps of 0 or 1 (each subdomain a
+ *                    contiguous node range of at most 16 nodes)
+ *   h_bc_mask        uint8[n_nodes] bit c set = A component c (0=x,1=y,2=z) is
+ *                    fixed to 0 at that node (A.n = 0 on the box faces, Sec. 3)
+ * Builds the block-sparse pattern on the device.  ECT_ERR_MESH on an index
+ * out of range or a tet of non-positive volume. */
+int ect_set_mesh(ect_ctx* ctx, const double* h_xyz, int64_t n_nodes,
+                 const int32_t* h_tets, int64_t n_tets,
+                 const double* h_sigma, const double* h_nu,
+                 const double* h_sigma_d, const double* h_nu_d,
+                 const int32_t* h_block_of_node, const uint8_t* h_bc_mask);
+
+/* Frequency (Hz), nu_tilde = 1/mu_tilde of the Coulomb-gauge penalty (Eq. CGCdiv
+ * text) and the V-gauge penalty factor delta of Sec. 4 (1/m^2). */
+int ect_set_physics(ect_ctx* ctx, double freq_hz, double nu_tilde, double delta_gauge);
+
+/* Step 3-4 of Sec. 3: assemble the matrix of configuration `which` from the
+ * element forms L11, L12, L21, L22 (Sec. 2-3, the coupled form after scaling the
+ * V equation by -1/(i omega), with the -i omega sigma mass term in L11 and the
+ * delta sigma V gauge penalty in L22), race-free into 4x4 complex blocks (BSR),
+ * eliminate A.n = 0, set identity V rows at nodes outside the conductor, and
+ * build the symmetric diagonal scaling.  precision_mask (ECT_F64|ECT_F32)
+ * selects the scaled copies kept for the solver (F64 is always built). */
+int ect_assemble(ect_ctx* ctx, int which, int precision_mask);
+
+/* Subdomain-block preconditioner (the paper's partition of Sec. 3 re-expressed
+ * as one dense block per subdomain): inverts the diagonal blocks of the scaled
+ * matrix over each subdomain.  precision_mask as for ect_assemble. */
+int ect_precond_setup(ect_ctx* ctx, int which, int precision_mask);
+
+/* Sizes of the assembled pattern: rows = n_nodes block rows, nnzb blocks. */
+int ect_matrix_info(const ect_ctx* ctx, int64_t* n_block_rows, int64_t* nnzb);
+
+/* Copy the assembled, constrained, unscaled FP64 matrix of `which` to the host:
+ * h_row_ptr int32[n+1], h_col int32[nnzb], h_val double[nnzb][4][4][2]
+ * (block row-major: [row comp][col comp]).  Any pointer may be NULL. */
+int ect_matrix_copy(ect_ctx* ctx, int which, int32_t* h_row_ptr, int32_t* h_col, double* h_val);
+
+/* Copy the scaling vector t (double[4*n_nodes]), S = diag(t) M diag(t). */
+int ect_scaling_copy(ect_ctx* ctx, int which, double* h_t);
+
+/* y = M x for k vectors (unscaled matrix, FP64; or the FP32 copy of the
+ * unscaled matrix when precision == ECT_F32, in which case d_x, d_y are
+ * complex64).  d_x, d_y: [k][n_nodes][4], must not overlap. */
+int ect_spmv(ect_ctx* ctx, int which, int precision, const void* d_x, void* d_y, int k);
+
+/* z = blockdiag(S_ss)^-1 r on the scaled system for k vectors ([k][n][4]). */
+int ect_precond_apply(ect_ctx* ctx, int which, int precision, const void* d_r, void* d_z, int k);
+
+/* Classical Gram-Schmidt applied twice (the Arnoldi step of GMRES):
+ * d_V holds j orthonormal complex vectors of length n (d_V[i*n + e]),
+ * d_w one vector that is overwritten by its projection off span(V);
+ * h_h receives the j accumulated coefficients (complex128) and *h_beta the
+ * norm of the result.  precision selects complex128 or complex64 storage. */
+int ect_cgs2(ect_ctx* ctx, int precision, const void* d_V, int j, int64_t n, void* d_w,
+             double* h_h, double* h_beta);
+
+/* Step 6 source term: load vectors of one coil at k probe positions
+ * (Sec. 3: mass matrix times the interpolated J of Sec. 4, restricted to the
+ * coil, each tet weighted by its volume fraction in the coil).
+ * h_z_probe double[k]; d_rhs complex128 [k][n_nodes][4] (V rows zero,
+ * constrained dofs zero). */
+int ect_coil_rhs(ect_ctx* ctx, const ect_coil* coil, const double* h_z_probe, int k, void* d_rhs);
+
+/* Step 5-6: solve M x = b for k right-hand sides of configuration `which`
+ * with preconditioned flexible GMRES (or the mixed FP64/FP32 scheme).
+ * d_rhs, d_x complex128 [k][n_nodes][4]; d_x need not be initialised.
+ * Needs ect_assemble and ect_precond_setup (with ECT_F32 for mixed mode). */
+int ect_solve(ect_ctx* ctx, int which, const void* d_rhs, void* d_x, int k,
+              const ect_options* opt, ect_stats* stats);
+
+/* Eq. impedkl read as the discrete reciprocity identity:
+ *   dZ_kl = (i omega / (I_k I_l)) u_k^0^T (M_d - M_0) u_l^d,
+ * reduced over the defect tets.  d_u0, d_ud complex128 [2][n_nodes][4] (coil
+ * 1 and 2 solutions of the vacuum and defect systems); h_current[2] the coil
+ * currents; h_dz receives complex128 [2][2].  If h_dz_emf is not NULL it
+ * receives the coil-EMF difference -(i omega/(I_k I_l)) b_k^T (u_l^d - u_l^0)
+ * computed from d_b (complex128 [2][n_nodes][4]) as a cross-check. */
+int ect_delta_z(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_b,
+                const double* h_current, double* h_dz, double* h_dz_emf);
+
+/* Step 6-7 for a probe scan: for each of n_pos positions build both coils'
+ * sources, solve the vacuum and defect systems (4 solves per position,
+ * batched), and reduce Delta Z.  h_dz receives complex128 [n_pos][2][2].
+ * Needs both matrices assembled and their preconditioners set up. */
+int ect_impedance(ect_ctx* ctx, const ect_coil coils[2], const double* h_z_pos, int n_pos,
+                  const ect_options* opt, double* h_dz, ect_stats* stats);
+
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECT_H */

@@ -1,0 +1,151 @@
+// Kernel (a): race-free P1 assembly of the A-V system into 4x4 complex blocks.
+//
+// For tet K with volume |K| and barycentric gradients g_a, the coupled form
+// of Sec. 2 (L11 + L12 + L21 + L22 after the V equation is scaled by
+// -1/(i omega), with the -i omega sigma mass term inside L11 and the gauge
+// penalty delta sigma V of Sec. 4 inside L22) gives the node-pair block
+// (test node a, trial node b), rows/cols ordered (A_x, A_y, A_z, V):
+//   AA_pq = |K| [nu (d_pq g_a.g_b - g_aq g_bp) + nu_t g_ap g_bq]
+//           - i omega sigma |K| (1 + d_ab)/20 d_pq
+//   AV_p  = -sigma |K| g_bp / 4,        VA_q = -sigma |K| g_aq / 4
+//   VV    = -(sigma/(i omega)) |K| (g_a.g_b + delta (1 + d_ab)/20)
+// One thread owns one block and sums the contributions of every tet that
+// shares its node pair (the list built in mesh_setup.cu), so no two threads
+// write the same value and the summation order is fixed.  The constraints
+// follow: A.n = 0 by elimination (zero row and column, unit diagonal) and
+// the identity on V at nodes that touch no conducting tet.  Finally the
+// symmetric scaling S = T M T with T = diag(|M_ii|^-1/2) is formed in FP64
+// and, on request, rounded to an FP32 copy.
+#include "common.cuh"
+
+namespace {
+
+__device__ __forceinline__ int row_of_slot(const int32_t* __restrict__ row_ptr, int64_t n_rows, int slot) {
+    int lo = 0, hi = (int)n_rows - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (row_ptr[mid] <= slot) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128) k_assemble(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ slot_ptr,
+    const uint32_t* __restrict__ entries, const double* __restrict__ geo, const double* __restrict__ sigma,
+    const double* __restrict__ nu, const uint8_t* __restrict__ fixmask, int64_t n_rows, int64_t nnzb,
+    double nu_t, double omega, double delta, double2* __restrict__ val) {
+    int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (slot >= nnzb) return;
+    double re[16], im[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) re[e] = im[e] = 0.0;
+    const double inv_omega = 1.0 / omega;
+    for (int32_t q = slot_ptr[slot]; q < slot_ptr[slot + 1]; ++q) {
+        uint32_t ent = entries[q];
+        int64_t t = ent >> 4;
+        int a = (ent >> 2) & 3, b = ent & 3;
+        const double* g = geo + 16 * t;
+        double vol = g[0];
+        double ga[3] = {g[1 + 3 * a], g[2 + 3 * a], g[3 + 3 * a]};
+        double gb[3] = {g[1 + 3 * b], g[2 + 3 * b], g[3 + 3 * b]};
+        double s = sigma[t], n = nu[t];
+        double gab = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+        double mass = (a == b ? 2.0 : 1.0) / 20.0;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                double cc = (p == r ? gab : 0.0) - ga[r] * gb[p];
+                re[4 * p + r] += vol * (n * cc + nu_t * ga[p] * gb[r]);
+            }
+            im[5 * p] -= omega * s * vol * mass;
+            re[4 * p + 3] -= 0.25 * s * vol * gb[p];
+            re[12 + p] -= 0.25 * s * vol * ga[p];
+        }
+        im[15] += s * inv_omega * vol * (gab + delta * mass);
+    }
+    int row = row_of_slot(row_ptr, n_rows, (int)slot);
+    int cl = col[slot];
+    unsigned fr = fixmask[row], fc = fixmask[cl];
+    double2* out = val + 16 * slot;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            double2 v = make_double2(re[4 * p + r], im[4 * p + r]);
+            if (((fr >> p) & 1u) || ((fc >> r) & 1u)) v = make_double2(0.0, 0.0);
+            if (row == cl && p == r && ((fr >> p) & 1u)) v = make_double2(1.0, 0.0);
+            out[4 * p + r] = v;
+        }
+    }
+}
+
+__global__ void k_scaling(const double2* __restrict__ val, const int32_t* __restrict__ diag_slot, int64_t n_rows,
+                          double* __restrict__ t) {
+    int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= 4 * n_rows) return;
+    int64_t row = d >> 2;
+    int p = (int)(d & 3);
+    double2 m = val[16 * (int64_t)diag_slot[row] + 5 * p];
+    double a = sqrt(m.x * m.x + m.y * m.y);
+    t[d] = a > 0.0 ? 1.0 / sqrt(a) : 1.0;
+}
+
+__global__ void k_scale_matrix(const double2* __restrict__ val, const int32_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ col, const double* __restrict__ t, int64_t n_rows,
+                               int64_t nnzb, double2* __restrict__ sval, float2* __restrict__ sval32) {
+    int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (slot >= nnzb) return;
+    int row = row_of_slot(row_ptr, n_rows, (int)slot);
+    int cl = col[slot];
+    double tr[4], tc[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        tr[p] = t[4 * (int64_t)row + p];
+        tc[p] = t[4 * (int64_t)cl + p];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            double2 m = val[16 * slot + 4 * p + r];
+            double s = tr[p] * tc[r];
+            double2 v = make_double2(m.x * s, m.y * s);
+            sval[16 * slot + 4 * p + r] = v;
+            if (sval32) sval32[16 * slot + 4 * p + r] = make_float2((float)v.x, (float)v.y);
+        }
+}
+
+}  // namespace
+
+void assemble_matrix(ect_ctx* c, int which, int precision_mask) {
+    ECT_REQUIRE(c->mesh_set, ECT_ERR_STATE, "ect_set_mesh must come before ect_assemble");
+    ECT_REQUIRE(c->physics_set, ECT_ERR_STATE, "ect_set_physics must come before ect_assemble");
+    ECT_REQUIRE(which == ECT_VACUUM || which == ECT_DEFECT, ECT_ERR_ARG, "which must be ECT_VACUUM or ECT_DEFECT");
+    ECT_REQUIRE((precision_mask & ~(ECT_F64 | ECT_F32)) == 0, ECT_ERR_ARG, "bad precision mask");
+    Matrix& M = c->mat[which];
+    cudaStream_t st = c->stream;
+    const int64_t nnzb = c->nnzb, N = c->n_nodes;
+    M.val.alloc(sizeof(double2) * 16 * nnzb);
+    M.sval.alloc(sizeof(double2) * 16 * nnzb);
+    M.t.alloc(sizeof(double) * 4 * N);
+    bool f32 = (precision_mask & ECT_F32) != 0;
+    if (f32) M.sval32.alloc(sizeof(float2) * 16 * nnzb);
+    else M.sval32.release();
+    k_assemble<<<grid_for(nnzb, 128), 128, 0, st>>>(
+        c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), c->slot_ptr.as<int32_t>(), c->entries.as<uint32_t>(),
+        c->geo.as<double>(), M.sigma.as<double>(), M.nu.as<double>(), M.fixmask.as<uint8_t>(), N, nnzb,
+        c->nu_tilde, c->omega, c->delta, M.val.as<double2>());
+    ECT_CHECK_LAUNCH();
+    k_scaling<<<grid_for(4 * N, 256), 256, 0, st>>>(M.val.as<double2>(), c->diag_slot.as<int32_t>(), N,
+                                                    M.t.as<double>());
+    ECT_CHECK_LAUNCH();
+    k_scale_matrix<<<grid_for(nnzb, 128), 128, 0, st>>>(M.val.as<double2>(), c->row_ptr.as<int32_t>(),
+                                                        c->col.as<int32_t>(), M.t.as<double>(), N, nnzb,
+                                                        M.sval.as<double2>(), f32 ? M.sval32.as<float2>() : nullptr);
+    ECT_CHECK_LAUNCH();
+    M.assembled = true;
+    M.has_f32 = f32;
+    M.pc_f64 = M.pc_f32 = false;
+}

@@ -1,0 +1,226 @@
+// Shared device helpers and the library context of the eddy-current solver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ect.h"
+
+// ----------------------------------------------------------------------------
+// complex arithmetic on double2 / float2 (x = re, y = im)
+// ----------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<float> { using type = float2; };
+template <typename T> using C = typename cplx<T>::type;
+
+__host__ __device__ __forceinline__ double2 mk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ float2 mk(float r, float i) { return make_float2(r, i); }
+template <typename T> __host__ __device__ __forceinline__ C<T> czero() { return mk(T(0), T(0)); }
+
+// acc += a * b
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfma_conj(double2& acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma_conj(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+__device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_d(double2 a) { return a; }
+template <typename T> __device__ __forceinline__ C<T> from_d(double2 a);
+template <> __device__ __forceinline__ double2 from_d<double>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_d<float>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// warp sum of a double
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ----------------------------------------------------------------------------
+// error handling
+// ----------------------------------------------------------------------------
+struct EctError {
+    int code;
+    std::string msg;
+};
+
+#define ECT_CUDA(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            throw EctError{_e == cudaErrorMemoryAllocation ? ECT_ERR_OOM : ECT_ERR_CUDA,       \
+                           std::string(#call) + ": " + cudaGetErrorString(_e)};               \
+        }                                                                                     \
+    } while (0)
+
+#define ECT_CHECK_LAUNCH() ECT_CUDA(cudaGetLastError())
+
+#define ECT_REQUIRE(cond, code, msg)                  \
+    do {                                              \
+        if (!(cond)) throw EctError{(code), (msg)};   \
+    } while (0)
+
+inline unsigned grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+// ----------------------------------------------------------------------------
+// device buffer
+// ----------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    void alloc(size_t nbytes) {
+        if (nbytes == bytes && p) return;
+        release();
+        if (nbytes == 0) return;
+        ECT_CUDA(cudaMalloc(&p, nbytes));
+        bytes = nbytes;
+    }
+    void ensure(size_t nbytes) {
+        if (nbytes > bytes) alloc(nbytes);
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// ----------------------------------------------------------------------------
+// context
+// ----------------------------------------------------------------------------
+struct Matrix {
+    bool assembled = false;
+    bool has_f32 = false;
+    bool pc_f64 = false, pc_f32 = false;
+    DevBuf sigma, nu;      // per tet, effective coefficients of this configuration
+    DevBuf fixmask;        // uint8 per node: bits 0-2 Dirichlet A, bit 3 V identity
+    DevBuf val;            // double2[nnzb*16] unscaled, constrained
+    DevBuf sval;           // double2[nnzb*16] scaled  S = T M T
+    DevBuf sval32;         // float2 [nnzb*16] scaled
+    DevBuf t;              // double[4N] scaling
+    DevBuf pinv;           // double2 block inverses (column-major per block)
+    DevBuf pinv32;         // float2  block inverses
+    void reset() {
+        assembled = has_f32 = pc_f64 = pc_f32 = false;
+        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &t, &pinv, &pinv32}) b->release();
+    }
+};
+
+struct Workspace;  // Krylov workspace (krylov.cu)
+
+struct ect_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    // physics
+    double freq = 1.0e5, omega = 2.0 * 3.14159265358979323846 * 1.0e5;
+    double nu_tilde = 0.0, delta = 1.0;
+    bool physics_set = false;
+    // mesh
+    bool mesh_set = false;
+    int64_t n_nodes = 0, n_tets = 0, nnzb = 0, n_blocks = 0, n_entries = 0;
+    int max_block_nodes = 0;
+    DevBuf xyz;            // double[N*3]
+    DevBuf tets;           // int32[T*4]
+    DevBuf geo;            // double[T*16]: vol, g0..g3 (xyz), pad
+    DevBuf bc;             // uint8[N]
+    DevBuf row_ptr;        // int32[N+1]
+    DevBuf col;            // int32[nnzb]
+    DevBuf diag_slot;      // int32[N]
+    DevBuf slot_ptr;       // int32[nnzb+1]
+    DevBuf entries;        // uint32[16T]: tet<<4 | a<<2 | b
+    DevBuf block_ptr;      // int32[n_blocks+1] node offsets
+    DevBuf pinv_off;       // int64[n_blocks+1] offsets (in complex entries) of block inverses
+    int64_t pinv_total = 0;
+    DevBuf omega_d;        // int32 list of defect tets
+    int64_t n_omega_d = 0;
+    std::vector<int32_t> h_block_ptr;
+    Matrix mat[2];
+    Workspace* ws = nullptr;
+    // scratch
+    DevBuf scratch;        // reduction partials etc.
+    DevBuf pinned;         // host-visible small results
+    void* h_pinned = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// shared scratch (partials) helper
+inline double* ctx_scratch(ect_ctx* c, size_t doubles) {
+    c->scratch.ensure(doubles * sizeof(double));
+    return c->scratch.as<double>();
+}
+
+// ----------------------------------------------------------------------------
+// cross-file entry points (implemented in the .cu files)
+// ----------------------------------------------------------------------------
+void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                const double* sigma, const double* nu, const double* sigma_d, const double* nu_d,
+                const int32_t* block_of_node, const uint8_t* bc_mask);
+void assemble_matrix(ect_ctx* c, int which, int precision_mask);
+void precond_setup(ect_ctx* c, int which, int precision_mask);
+
+// y = A x for k vectors; A = unscaled F64 (scaled=false) or scaled S (scaled=true)
+void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, int k, int64_t ldx,
+              int rhs_tile, const int* active);
+void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t ldx, int rhs_tile,
+              const int* active);
+void precond_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld,
+                       int rhs_tile, const int* active);
+void precond_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld,
+                       int rhs_tile, const int* active);
+void coil_rhs(ect_ctx* c, const ect_coil& coil, const double* h_z, int k, double2* d_rhs);
+void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b, const double* cur,
+             int n_pos, double* h_dz, double* h_dz_emf);
+void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const ect_options& opt,
+           ect_stats* st);
+void cgs2_entry(ect_ctx* c, int precision, const void* V, int j, int64_t n, void* w, double* h,
+                double* beta);
+void workspace_free(ect_ctx* c);

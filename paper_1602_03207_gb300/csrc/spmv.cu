@@ -1,0 +1,138 @@
+// Kernel (b): BSR (4x4 complex blocks) SpMV and multi-right-hand-side SpMM.
+//
+// y_r = A x_r for r in a tile of KT right-hand sides.  One thread owns one
+// scalar row (node i, component p) and KT accumulators: it streams row p of
+// each of the node's blocks once (64 B in FP64, 32 B in FP32, vector loads)
+// and applies it to the KT vectors, so the matrix is read once per tile of
+// right-hand sides.  The four threads of a node read one block's four rows,
+// which are contiguous, and broadcast-share the x segment of each column
+// node.  Vectors are stored [k][4N] with leading dimension ld.
+#include "common.cuh"
+
+namespace {
+
+template <int KT>
+__global__ void __launch_bounds__(256) k_spmv_f64(const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const double2* __restrict__ val, const double2* __restrict__ x,
+                                                  double2* __restrict__ y, int64_t n_rows, int k, int64_t ld,
+                                                  const int* __restrict__ active) {
+    int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= 4 * n_rows) return;
+    const int row = (int)(d >> 2), p = (int)(d & 3);
+    const int r0 = blockIdx.y * KT;
+    bool on[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    double2 acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = make_double2(0.0, 0.0);
+    const int s1 = row_ptr[row + 1];
+    for (int s = row_ptr[row]; s < s1; ++s) {
+        const int c = col[s];
+        const double2* v = val + 16 * (int64_t)s + 4 * p;
+        const double2 a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            if (!on[q]) continue;
+            const double2* xv = x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c;
+            cfma(acc[q], a0, xv[0]);
+            cfma(acc[q], a1, xv[1]);
+            cfma(acc[q], a2, xv[2]);
+            cfma(acc[q], a3, xv[3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (on[q]) y[(int64_t)(r0 + q) * ld + d] = acc[q];
+}
+
+template <int KT>
+__global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const float2* __restrict__ val, const float2* __restrict__ x,
+                                                  float2* __restrict__ y, int64_t n_rows, int k, int64_t ld,
+                                                  const int* __restrict__ active) {
+    int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= 4 * n_rows) return;
+    const int row = (int)(d >> 2), p = (int)(d & 3);
+    const int r0 = blockIdx.y * KT;
+    bool on[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    float2 acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = make_float2(0.f, 0.f);
+    const int s1 = row_ptr[row + 1];
+    for (int s = row_ptr[row]; s < s1; ++s) {
+        const int c = col[s];
+        const float4* v = reinterpret_cast<const float4*>(val + 16 * (int64_t)s + 4 * p);
+        const float4 v01 = v[0], v23 = v[1];
+        const float2 a0 = make_float2(v01.x, v01.y), a1 = make_float2(v01.z, v01.w);
+        const float2 a2 = make_float2(v23.x, v23.y), a3 = make_float2(v23.z, v23.w);
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            if (!on[q]) continue;
+            const float4* xv = reinterpret_cast<const float4*>(x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c);
+            const float4 x01 = xv[0], x23 = xv[1];
+            cfma(acc[q], a0, make_float2(x01.x, x01.y));
+            cfma(acc[q], a1, make_float2(x01.z, x01.w));
+            cfma(acc[q], a2, make_float2(x23.x, x23.y));
+            cfma(acc[q], a3, make_float2(x23.z, x23.w));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (on[q]) y[(int64_t)(r0 + q) * ld + d] = acc[q];
+}
+
+int pick_tile(int k, int rhs_tile) {
+    int kt = rhs_tile > 0 ? rhs_tile : 8;
+    if (kt > k) kt = k;
+    if (kt >= 8) return 8;
+    if (kt >= 4) return 4;
+    if (kt >= 2) return 2;
+    return 1;
+}
+
+}  // namespace
+
+void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, int k, int64_t ldx, int rhs_tile,
+              const int* active) {
+    Matrix& M = c->mat[which];
+    ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "matrix not assembled");
+    const double2* val = scaled ? M.sval.as<double2>() : M.val.as<double2>();
+    const int64_t N = c->n_nodes;
+    const int kt = pick_tile(k, rhs_tile);
+    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
+    cudaStream_t st = c->stream;
+    const int32_t* rp = c->row_ptr.as<int32_t>();
+    const int32_t* cl = c->col.as<int32_t>();
+    switch (kt) {
+        case 8: k_spmv_f64<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+        case 4: k_spmv_f64<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+        case 2: k_spmv_f64<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+        default: k_spmv_f64<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+    }
+    ECT_CHECK_LAUNCH();
+}
+
+void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t ldx, int rhs_tile,
+              const int* active) {
+    Matrix& M = c->mat[which];
+    ECT_REQUIRE(M.assembled && M.has_f32, ECT_ERR_STATE, "FP32 matrix not assembled (use ECT_F32 in ect_assemble)");
+    const int64_t N = c->n_nodes;
+    const int kt = pick_tile(k, rhs_tile);
+    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
+    cudaStream_t st = c->stream;
+    const int32_t* rp = c->row_ptr.as<int32_t>();
+    const int32_t* cl = c->col.as<int32_t>();
+    const float2* val = M.sval32.as<float2>();
+    switch (kt) {
+        case 8: k_spmv_f32<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+        case 4: k_spmv_f32<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+        case 2: k_spmv_f32<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+        default: k_spmv_f32<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
+    }
+    ECT_CHECK_LAUNCH();
+}

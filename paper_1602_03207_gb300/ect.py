@@ -1,0 +1,279 @@
+"""Thin Python binding of the C ABI in include/ect.h (argument marshalling only).
+
+Every computation runs in libect.so.  Host arrays are numpy arrays; device
+buffers are torch CUDA tensors (complex128 or complex64, contiguous) whose
+data pointers are handed to the library.  There is no CPU fallback: if the
+library is missing or fails to load, every entry point raises.
+
+Each Context owns a dedicated CUDA stream; calls order themselves after the
+caller's current torch stream and make it wait for the library's work, so
+tensors can be used as ordinary torch tensors before and after a call.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libect.so")
+
+ECT_OK = 0
+ECT_ERR_ARG, ECT_ERR_MESH, ECT_ERR_CUDA, ECT_ERR_OOM = 1, 2, 3, 4
+ECT_ERR_NOT_CONVERGED, ECT_ERR_BREAKDOWN, ECT_ERR_TIMEOUT, ECT_ERR_STATE = 5, 6, 7, 8
+ECT_VACUUM, ECT_DEFECT = 0, 1
+ECT_F64, ECT_F32 = 1, 2
+ECT_MODE_F64, ECT_MODE_MIXED = 0, 1
+
+_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_CUDA", 4: "ERR_OOM", 5: "ERR_NOT_CONVERGED",
+          6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
+
+# every symbol include/ect.h declares
+EXPORTS = ["ect_default_options", "ect_create", "ect_destroy", "ect_last_error", "ect_set_mesh",
+           "ect_set_physics", "ect_assemble", "ect_precond_setup", "ect_matrix_info", "ect_matrix_copy",
+           "ect_scaling_copy", "ect_spmv", "ect_precond_apply", "ect_cgs2", "ect_coil_rhs", "ect_solve",
+           "ect_delta_z", "ect_impedance"]
+
+
+class EctError(RuntimeError):
+    def __init__(self, code, msg, stats=None):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+        self.stats = stats
+
+
+class Coil(ctypes.Structure):
+    _fields_ = [("r_in", ctypes.c_double), ("r_out", ctypes.c_double), ("length", ctypes.c_double),
+                ("z_offset", ctypes.c_double), ("J_e", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("mode", ctypes.c_int), ("inner_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("rhs_tile", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("relres_max", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libect.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with __graft_entry__.build() "
+                           "or python paper_1602_03207_gb300/build.py")
+    L = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "ect_default_options": (None, [ctypes.POINTER(Options)]),
+        "ect_create": (I, [ctypes.POINTER(P), P]),
+        "ect_destroy": (None, [P]),
+        "ect_last_error": (ctypes.c_char_p, [P]),
+        "ect_set_mesh": (I, [P, P, I64, P, I64, P, P, P, P, P, P]),
+        "ect_set_physics": (I, [P, D, D, D]),
+        "ect_assemble": (I, [P, I, I]),
+        "ect_precond_setup": (I, [P, I, I]),
+        "ect_matrix_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "ect_matrix_copy": (I, [P, I, P, P, P]),
+        "ect_scaling_copy": (I, [P, I, P]),
+        "ect_spmv": (I, [P, I, I, P, P, I]),
+        "ect_precond_apply": (I, [P, I, I, P, P, I]),
+        "ect_cgs2": (I, [P, I, P, I, I64, P, P, P]),
+        "ect_coil_rhs": (I, [P, ctypes.POINTER(Coil), P, I, P]),
+        "ect_solve": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
+        "ect_delta_z": (I, [P, P, P, P, P, P, P]),
+        "ect_impedance": (I, [P, ctypes.POINTER(Coil), P, I, ctypes.POINTER(Options), P, ctypes.POINTER(Stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def default_options(**kw):
+    o = Options()
+    load_library().ect_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    """Host pointer of a contiguous numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(t):
+    """Device pointer of a contiguous torch CUDA tensor."""
+    assert t.is_cuda and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def coil(c):
+    """ect_coil from an object with r_in, r_out, length, z_offset, J_e."""
+    return Coil(c.r_in, c.r_out, c.length, c.z_offset, c.J_e)
+
+
+class Context:
+    """One ect_ctx bound to its own CUDA stream on the current device."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self.L = load_library()
+        self.stream = torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        rc = self.L.ect_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != ECT_OK:
+            raise EctError(rc, self.L.ect_last_error(None).decode())
+        self.h = h
+        self.n_nodes = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ect_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ordering with the caller's torch stream
+    def _call(self, fn, *args, stats=None):
+        cur = self._torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        rc = fn(self.h, *args)
+        cur.wait_stream(self.stream)
+        if rc != ECT_OK:
+            raise EctError(rc, self.L.ect_last_error(self.h).decode(), stats)
+        return rc
+
+    # ---- ect_set_mesh / ect_set_physics ------------------------------------
+    def set_mesh(self, xyz, tets, sigma, nu, sigma_d, nu_d, block_of_node, bc_mask):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        nu = np.ascontiguousarray(nu, dtype=np.float64)
+        sd = None if sigma_d is None else np.ascontiguousarray(sigma_d, dtype=np.float64)
+        nd = None if nu_d is None else np.ascontiguousarray(nu_d, dtype=np.float64)
+        bon = np.ascontiguousarray(block_of_node, dtype=np.int32)
+        bc = np.ascontiguousarray(bc_mask, dtype=np.uint8)
+        self._call(self.L.ect_set_mesh, _ptr(xyz), xyz.shape[0], _ptr(tets), tets.shape[0], _ptr(sigma),
+                   _ptr(nu), _ptr(sd), _ptr(nd), _ptr(bon), _ptr(bc))
+        self.n_nodes = xyz.shape[0]
+
+    def set_physics(self, freq_hz, nu_tilde, delta_gauge):
+        self._call(self.L.ect_set_physics, float(freq_hz), float(nu_tilde), float(delta_gauge))
+
+    def load_problem(self, p):
+        """set_mesh + set_physics from an object with the fields of a problem description."""
+        m = p.mesh
+        self.set_mesh(m.xyz, m.tets, p.sigma, p.nu, p.sigma_d, p.nu_d, m.block_of_node, m.bc_mask)
+        self.set_physics(p.freq, p.nu_tilde, p.delta)
+
+    # ---- assembly and preconditioner ---------------------------------------
+    def assemble(self, which, precision_mask=ECT_F64):
+        self._call(self.L.ect_assemble, int(which), int(precision_mask))
+
+    def precond_setup(self, which, precision_mask=ECT_F64):
+        self._call(self.L.ect_precond_setup, int(which), int(precision_mask))
+
+    def matrix_info(self):
+        n, nb = ctypes.c_int64(), ctypes.c_int64()
+        rc = self.L.ect_matrix_info(self.h, ctypes.byref(n), ctypes.byref(nb))
+        if rc != ECT_OK:
+            raise EctError(rc, "matrix_info")
+        return n.value, nb.value
+
+    def matrix_copy(self, which):
+        n, nb = self.matrix_info()
+        rp = np.empty(n + 1, dtype=np.int32)
+        col = np.empty(nb, dtype=np.int32)
+        val = np.empty((nb, 4, 4, 2), dtype=np.float64)
+        self._call(self.L.ect_matrix_copy, int(which), _ptr(rp), _ptr(col), _ptr(val))
+        return rp, col, val[..., 0] + 1j * val[..., 1]
+
+    def scaling_copy(self, which):
+        t = np.empty(4 * self.n_nodes, dtype=np.float64)
+        self._call(self.L.ect_scaling_copy, int(which), _ptr(t))
+        return t
+
+    # ---- kernels -------------------------------------------------------------
+    def spmv(self, which, x, y, k=1, precision=ECT_F64):
+        self._call(self.L.ect_spmv, int(which), int(precision), _dptr(x), _dptr(y), int(k))
+
+    def precond_apply(self, which, r, z, k=1, precision=ECT_F64):
+        self._call(self.L.ect_precond_apply, int(which), int(precision), _dptr(r), _dptr(z), int(k))
+
+    def cgs2(self, V, w, precision=ECT_F64):
+        """V: (j, n) tensor of orthonormal rows, w: (n,) tensor (overwritten)."""
+        j, n = V.shape
+        h = np.empty((j, 2), dtype=np.float64)
+        beta = np.empty(1, dtype=np.float64)
+        self._call(self.L.ect_cgs2, int(precision), _dptr(V), int(j), int(n), _dptr(w), _ptr(h), _ptr(beta))
+        return h[:, 0] + 1j * h[:, 1], float(beta[0])
+
+    def coil_rhs(self, c, z_probe, out):
+        z = np.ascontiguousarray(np.atleast_1d(z_probe), dtype=np.float64)
+        cc = coil(c)
+        self._call(self.L.ect_coil_rhs, ctypes.byref(cc), _ptr(z), int(z.size), _dptr(out))
+
+    def solve(self, which, rhs, x, k=1, options=None):
+        o = options if options is not None else default_options()
+        st = Stats()
+        try:
+            self._call(self.L.ect_solve, int(which), _dptr(rhs), _dptr(x), int(k), ctypes.byref(o),
+                       ctypes.byref(st), stats=st)
+        except EctError as e:
+            e.stats = st.as_dict()
+            raise
+        return st.as_dict()
+
+    def delta_z(self, u0, ud, b, currents):
+        cur = np.ascontiguousarray(currents, dtype=np.float64)
+        dz = np.empty((2, 2, 2), dtype=np.float64)
+        dze = np.empty((2, 2, 2), dtype=np.float64)
+        self._call(self.L.ect_delta_z, _dptr(u0), _dptr(ud), None if b is None else _dptr(b), _ptr(cur),
+                   _ptr(dz), _ptr(dze) if b is not None else None)
+        out = dz[..., 0] + 1j * dz[..., 1]
+        return out, (dze[..., 0] + 1j * dze[..., 1]) if b is not None else None
+
+    def impedance(self, coils, z_pos, options=None):
+        z = np.ascontiguousarray(np.atleast_1d(z_pos), dtype=np.float64)
+        arr = (Coil * 2)(coil(coils[0]), coil(coils[1]))
+        o = options if options is not None else default_options()
+        dz = np.empty((z.size, 2, 2, 2), dtype=np.float64)
+        st = Stats()
+        try:
+            self._call(self.L.ect_impedance, arr, _ptr(z), int(z.size), ctypes.byref(o), _ptr(dz),
+                       ctypes.byref(st), stats=st)
+        except EctError as e:
+            e.stats = st.as_dict()
+            raise
+        return dz[..., 0] + 1j * dz[..., 1], st.as_dict()

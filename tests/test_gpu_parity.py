@@ -1,0 +1,303 @@
+"""GPU parity: every step of the CUDA path against the FP64 CPU oracle.
+
+All GPU work goes through the C ABI (libect.so via the ctypes binding).
+Tolerances (derived in the design notes):
+  assembly / FP64 SpMV   |diff_ij| <= 1e-12 sqrt(|M_ii| |M_jj|)   (sum of ~24
+                          tet terms, each ~10 roundings of 1.1e-16)
+  FP32 scaled SpMV       <= 2e-6 relative (unit-scaled entries, 15 blocks/row)
+  block inverse apply    <= 1e-9 (FP64) / 1e-3 (FP32) relative: kappa(S_ss) eps
+  coil load              <= 1e-13 relative (point-in-coil decisions are exact)
+  solve                  ||T(b - M_oracle x)|| <= tol ||T b|| with the oracle's matrix
+  Delta Z                <= 1e-6 relative to the oracle (SuperLU) value
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import ect_inputs as E
+from oracle import fem, impedance, rhs, solve
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ect():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1602_03207_gb300 import build, ect as ect_mod
+    build.build()
+    ect_mod.load_library()
+    return ect_mod
+
+
+def small_problem(seed=1):
+    # 10 x 11 x 13 nodes, ragged 2x3x2 subdomains, jittered: several SpMV tiles and a ragged tail
+    return E.wall_loss_problem((10, 11, 13), (20e-3, 20e-3, 30e-3), (2, 3, 2), 0.15, seed, z_pos=(0.0,))
+
+
+def make_ctx(ect, p, f32=True):
+    ctx = ect.Context()
+    ctx.load_problem(p)
+    mask = ect.ECT_F64 | (ect.ECT_F32 if f32 else 0)
+    for w in (ect.ECT_VACUUM, ect.ECT_DEFECT):
+        ctx.assemble(w, mask)
+        ctx.precond_setup(w, mask)
+    return ctx
+
+
+def bsr_to_csr(rp, col, val):
+    n = rp.size - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    R = (4 * rows[:, None, None] + np.arange(4)[None, :, None]).repeat(4, axis=2)
+    Cc = (4 * col[:, None, None] + np.arange(4)[None, None, :]).repeat(4, axis=1)
+    return sp.csr_matrix((val.ravel(), (R.ravel(), Cc.ravel())), shape=(4 * n, 4 * n))
+
+
+def crand(rng, *shape):
+    return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+WHICH = {"vacuum": 0, "defect": 1}
+
+
+@pytest.fixture(scope="module")
+def small(ect):
+    p = small_problem()
+    ctx = make_ctx(ect, p)
+    M = {w: fem.system_matrix(p, w) for w in WHICH}
+    return p, ctx, M
+
+
+def test_assembly_matches_oracle(ect, small):
+    p, ctx, M = small
+    for w, wi in WHICH.items():
+        rp, col, val = ctx.matrix_copy(wi)
+        G = bsr_to_csr(rp, col, val)
+        O = M[w]
+        d = np.sqrt(np.abs(O.diagonal()))
+        D = (G - O).tocoo()
+        bound = 1e-12 * d[D.row] * d[D.col]
+        assert np.all(np.abs(D.data) <= bound + 1e-300), w
+        # every oracle entry is inside the BSR pattern, and the GPU matrix is symmetric
+        assert abs(G - G.T).max() <= 1e-13 * abs(G).max()
+
+
+def test_scaling_matches_oracle(ect, small):
+    p, ctx, M = small
+    for w, wi in WHICH.items():
+        t = ctx.scaling_copy(wi)
+        np.testing.assert_allclose(t, fem.scaling(M[w]), rtol=1e-13)
+
+
+def test_spmv_f64_batch(ect, small):
+    p, ctx, M = small
+    rng = np.random.default_rng(0)
+    n = 4 * p.mesh.n_nodes
+    for k in (1, 3, 9):
+        X = crand(rng, k, n)
+        x = dev(X)
+        y = torch.empty_like(x)
+        ctx.spmv(WHICH["defect"], x, y, k)
+        Y = y.cpu().numpy()
+        ref = (M["defect"] @ X.T).T
+        scale = np.abs(M["defect"]).max() * np.abs(X).max()
+        assert np.abs(Y - ref).max() <= 1e-13 * scale, k
+
+
+def test_spmv_f32_scaled(ect, small):
+    p, ctx, M = small
+    rng = np.random.default_rng(1)
+    n = 4 * p.mesh.n_nodes
+    t = fem.scaling(M["vacuum"])
+    S = fem.scaled(M["vacuum"], t)
+    X = crand(rng, 2, n)
+    x = dev(X, torch.complex64)
+    y = torch.empty_like(x)
+    ctx.spmv(WHICH["vacuum"], x, y, 2, precision=ect.ECT_F32)
+    ref = (S @ X.T).T
+    err = np.linalg.norm(y.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert err.max() <= 2e-6
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_precond_apply(ect, small, prec):
+    p, ctx, M = small
+    rng = np.random.default_rng(2)
+    n = 4 * p.mesh.n_nodes
+    t = fem.scaling(M["defect"])
+    S = fem.scaled(M["defect"], t)
+    P = solve.block_jacobi(S, p.mesh.block_of_node)
+    R = crand(rng, 3, n)
+    dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-9) if prec == "f64" else (torch.complex64, ect.ECT_F32, 1e-3))
+    r = dev(R, dt)
+    z = torch.empty_like(r)
+    ctx.precond_apply(WHICH["defect"], r, z, 3, precision=pr)
+    Z = z.cpu().numpy()
+    for q in range(3):
+        ref = solve.block_jacobi_apply(P, R[q])
+        assert np.linalg.norm(Z[q] - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,j", [(1000, 1), (70001, 7), (5003, 33)])
+def test_cgs2_matches_oracle(ect, prec, n, j):
+    rng = np.random.default_rng(n + j)
+    Vq, _ = np.linalg.qr(crand(rng, n, j))
+    w = crand(rng, n)
+    h_ref, w_ref, beta_ref = solve.cgs2(Vq, w)
+    dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-12) if prec == "f64" else (torch.complex64, ect.ECT_F32, 2e-5))
+    ctx = ect.Context()
+    V = dev(Vq.T, dt)
+    wd = dev(w, dt)
+    h, beta = ctx.cgs2(V, wd, precision=pr)
+    nw = np.linalg.norm(w)
+    assert np.abs(h - h_ref).max() <= tol * nw
+    assert abs(beta - beta_ref) <= tol * nw
+    assert np.linalg.norm(wd.cpu().numpy() - w_ref) <= tol * nw
+    ctx.close()
+
+
+def test_coil_rhs_matches_oracle(ect, small):
+    p, ctx, M = small
+    n = 4 * p.mesh.n_nodes
+    zs = np.array([0.0, 3.3e-3, -7.1e-3])
+    for c in p.coils:
+        out = torch.empty(3, n, dtype=torch.complex128, device="cuda")
+        ctx.coil_rhs(c, zs, out)
+        B = out.cpu().numpy()
+        for q, z in enumerate(zs):
+            ref = fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, c.as_tuple(), z), p, "vacuum")
+            assert np.abs(ref).max() > 0
+            assert np.abs(B[q] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def _solve_check(ect, p, ctx, M, which, opts, k=2):
+    n = 4 * p.mesh.n_nodes
+    B = np.stack([fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, c.as_tuple(), p.z_pos[0]), p, which)
+                  for c in p.coils][:k])
+    b = dev(B)
+    x = torch.empty_like(b)
+    st = ctx.solve(WHICH[which], b, x, k, opts)
+    X = x.cpu().numpy()
+    t = fem.scaling(M[which])
+    for q in range(k):
+        res = np.linalg.norm(t * (B[q] - M[which] @ X[q])) / np.linalg.norm(t * B[q])
+        assert res <= opts.tol * 1.0001, (q, res, st)
+    return X, st
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_solve_residual_with_oracle_matrix(ect, small, mode, graph):
+    p, ctx, M = small
+    opts = ect.default_options(tol=1e-10, restart=30, use_graph=graph,
+                               mode=ect.ECT_MODE_F64 if mode == "f64" else ect.ECT_MODE_MIXED, inner_iters=20)
+    for w in WHICH:
+        X, st = _solve_check(ect, p, ctx, M, w, opts)
+        assert st["converged"] == 2
+
+
+def test_solve_batch_equals_single(ect, small):
+    p, ctx, M = small
+    opts = ect.default_options(tol=1e-11)
+    X2, _ = _solve_check(ect, p, ctx, M, "defect", opts, k=2)
+    X1, _ = _solve_check(ect, p, ctx, M, "defect", opts, k=1)
+    assert np.linalg.norm(X2[0] - X1[0]) <= 1e-6 * np.linalg.norm(X1[0])
+
+
+def test_delta_z_kernel_on_oracle_solutions(ect, small):
+    """Kernel (e) alone: oracle solutions in, Delta Z out, against the oracle's global formula."""
+    p, ctx, M = small
+    b = [fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, c.as_tuple(), 0.0), p, "vacuum") for c in p.coils]
+    u0 = [solve.dense_solve(M["vacuum"], bk) for bk in b]
+    ud = [solve.dense_solve(M["defect"], bk) for bk in b]
+    I = [c.current for c in p.coils]
+    ref = impedance.delta_z_matrix(M["vacuum"], M["defect"], u0, ud, I, p.omega)
+    ref_emf = impedance.delta_z_emf_matrix(b, u0, ud, I, p.omega)
+    dz, dze = ctx.delta_z(dev(np.stack(u0)), dev(np.stack(ud)), dev(np.stack(b)), I)
+    assert np.abs(dz - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(dze - ref_emf).max() <= 1e-11 * np.abs(ref_emf).max()
+
+
+def test_impedance_c1_against_oracle_golden(ect):
+    g = json.load(open(os.path.join(HERE, "golden", "c1_oracle.json")))
+    ref = np.array([[complex(*g["dz"][k][l]) for l in range(2)] for k in range(2)])
+    p = E.make_config("c1")
+    ctx = make_ctx(ect, p)
+    for mode in (ect.ECT_MODE_F64, ect.ECT_MODE_MIXED):
+        opts = ect.default_options(tol=1e-10, mode=mode, inner_iters=20)
+        dz, st = ctx.impedance(p.coils, p.z_pos, opts)
+        err = np.abs(dz[0] - ref).max() / np.abs(ref).max()
+        assert err <= 1e-6, (mode, err, st)
+        assert st["converged"] == 4
+        assert abs(dz[0, 0, 1] - dz[0, 1, 0]) <= 1e-6 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_zero_contrast_gives_exact_zero(ect):
+    p = small_problem()
+    p.sigma_d = np.full_like(p.sigma_d, np.nan)
+    ctx = make_ctx(ect, p, f32=False)
+    dz, st = ctx.impedance(p.coils, p.z_pos, ect.default_options(tol=1e-10))
+    assert np.all(dz == 0)
+
+
+def test_coil_outside_mesh_gives_zero_solution(ect, small):
+    p, ctx, M = small
+    n = 4 * p.mesh.n_nodes
+    b = torch.empty(1, n, dtype=torch.complex128, device="cuda")
+    ctx.coil_rhs(p.coils[0], [1.0], b)                  # 1 m away along the axis
+    assert torch.count_nonzero(b).item() == 0
+    x = torch.full_like(b, 1.0)
+    st = ctx.solve(0, b, x, 1)
+    assert st["converged"] == 1 and torch.count_nonzero(x).item() == 0
+
+
+def test_not_converged_and_timeout_report(ect, small):
+    p, ctx, M = small
+    n = 4 * p.mesh.n_nodes
+    b = torch.empty(1, n, dtype=torch.complex128, device="cuda")
+    ctx.coil_rhs(p.coils[0], [0.0], b)
+    x = torch.empty_like(b)
+    with pytest.raises(ect.EctError) as e:
+        ctx.solve(0, b, x, 1, ect.default_options(restart=5, max_iters=5))
+    assert e.value.code == ect.ECT_ERR_NOT_CONVERGED and e.value.stats["iters"] == 5
+    assert 0 < e.value.stats["relres_max"] < 1
+    with pytest.raises(ect.EctError) as e:
+        ctx.solve(0, b, x, 1, ect.default_options(timeout_s=1e-12))
+    assert e.value.code == ect.ECT_ERR_TIMEOUT
+
+
+def test_bad_meshes_rejected(ect):
+    p = small_problem()
+    m = p.mesh
+    ctx = ect.Context()
+    bad = m.tets.copy()
+    bad[5, [1, 2]] = bad[5, [2, 1]]                         # inverted tet
+    with pytest.raises(ect.EctError) as e:
+        ctx.set_mesh(m.xyz, bad, p.sigma, p.nu, None, None, m.block_of_node, m.bc_mask)
+    assert e.value.code == ect.ECT_ERR_MESH
+    bad = m.tets.copy()
+    bad[0, 0] = m.n_nodes                                   # index out of range
+    with pytest.raises(ect.EctError) as e:
+        ctx.set_mesh(m.xyz, bad, p.sigma, p.nu, None, None, m.block_of_node, m.bc_mask)
+    assert e.value.code == ect.ECT_ERR_MESH
+    with pytest.raises(ect.EctError) as e:                  # one block of all nodes (> 16)
+        ctx.set_mesh(m.xyz, m.tets, p.sigma, p.nu, None, None, np.zeros(m.n_nodes, np.int32), m.bc_mask)
+    assert e.value.code == ect.ECT_ERR_ARG
+    with pytest.raises(ect.EctError) as e:                  # solve before assembly
+        ctx.set_mesh(m.xyz, m.tets, p.sigma, p.nu, None, None, m.block_of_node, m.bc_mask)
+        b = torch.zeros(1, 4 * m.n_nodes, dtype=torch.complex128, device="cuda")
+        ctx.solve(0, b, torch.empty_like(b), 1)
+    assert e.value.code == ect.ECT_ERR_STATE

@@ -72,6 +72,8 @@ typedef struct {
     int use_graph;      /* 1: replay each restart cycle as a captured CUDA graph           */
     int rhs_tile;       /* right-hand sides per SpMM/preconditioner pass (0 = auto)        */
     double timeout_s;   /* wall-clock limit of one solve call (0 = none)                  */
+    int reorth;         /* 0: always two Gram-Schmidt passes; 1: second pass only when the
+                           first removed more than half of ||w||^2 (default)             */
 } ect_options;
 
 typedef struct {
@@ -84,7 +86,8 @@ typedef struct {
 } ect_stats;
 
 /* Fill *opt with defaults: tol 1e-10, restart 30, max_iters 20000, F64 mode,
- * inner_iters 30, graphs on, automatic rhs tile, no timeout. */
+ * inner_iters 30, graphs on, automatic rhs tile, no timeout, selective
+ * reorthogonalisation. */
 void ect_default_options(ect_options* opt);
 
 /* Create a context bound to a CUDA stream (a cudaStream_t, may be NULL for the
@@ -130,8 +133,15 @@ int ect_assemble(ect_ctx* ctx, int which, int precision_mask);
 
 /* Subdomain-block preconditioner (the paper's partition of Sec. 3 re-expressed
  * as one dense block per subdomain): inverts the diagonal blocks of the scaled
- * matrix over each subdomain.  precision_mask as for ect_assemble. */
-int ect_precond_setup(ect_ctx* ctx, int which, int precision_mask);
+ * matrix over each subdomain.  precision_mask as for ect_assemble.
+ * coarse_group > 0 adds the conductor-V coarse space (two-level, additive):
+ * one coarse unknown per group of coarse_group consecutive subdomains that
+ * contains a conducting node, V = 1 on that group's conducting nodes (after
+ * the per-component gauge freedom of V noted in Sec. 4); its Galerkin matrix
+ * is inverted densely.  0 = block-Jacobi only; < 0 = automatic group (the
+ * smallest power of two giving at most 3072 coarse unknowns).  Coarse spaces
+ * above 16384 unknowns are rejected with ECT_ERR_ARG. */
+int ect_precond_setup(ect_ctx* ctx, int which, int precision_mask, int coarse_group);
 
 /* Sizes of the assembled pattern: rows = n_nodes block rows, nnzb blocks. */
 int ect_matrix_info(const ect_ctx* ctx, int64_t* n_block_rows, int64_t* nnzb);
@@ -173,6 +183,17 @@ int ect_coil_rhs(ect_ctx* ctx, const ect_coil* coil, const double* h_z_probe, in
  * Needs ect_assemble and ect_precond_setup (with ECT_F32 for mixed mode). */
 int ect_solve(ect_ctx* ctx, int which, const void* d_rhs, void* d_x, int k,
               const ect_options* opt, ect_stats* stats);
+
+/* Autotuner for batched solves of `which` with k right-hand sides d_rhs
+ * (complex128 [k][n_nodes][4]): times the SpMM and preconditioner right-hand-
+ * side tile (1, 2, 4, 8) with CUDA events, then runs full solves of d_rhs for
+ * each (restart, inner_iters) candidate of the mode in *base and keeps the
+ * fastest that converges.  *best receives *base with rhs_tile, restart and
+ * inner_iters replaced; stats of the winning solve go to *stats (may be NULL).
+ * d_work: complex128 [k][n_nodes][4] scratch for the solutions.  Costs one
+ * full solve per candidate; call it once per workload. */
+int ect_autotune(ect_ctx* ctx, int which, const void* d_rhs, void* d_work, int k, const ect_options* base,
+                 ect_options* best, ect_stats* stats);
 
 /* Eq. impedkl read as the discrete reciprocity identity:
  *   dZ_kl = (i omega / (I_k I_l)) u_k^0^T (M_d - M_0) u_l^d,

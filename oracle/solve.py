@@ -9,6 +9,11 @@ right-hand side per probe position (Sec. 3, Steps 5-6).  The oracle offers:
   * block_jacobi   the inverses of the diagonal blocks of the scaled matrix
                    over the node subdomains (the subdomain-block
                    preconditioner: z = blockdiag(S_ss)^-1 r);
+  * coarse_v       the conductor-V coarse space: one coarse unknown per
+                   group of `group` consecutive subdomains that touches the
+                   conductor, constant (=1 in the unscaled V) on that group's
+                   conducting nodes; E = Z^T S Z and the additive two-level
+                   preconditioner z = blockdiag(S_ss)^-1 r + Z E^-1 Z^T r;
   * fgmres         restarted flexible GMRES (Saad's algorithm) with
                    classical Gram-Schmidt applied twice, complex Givens
                    rotations for the Hessenberg least-squares problem, and a
@@ -56,6 +61,39 @@ def block_jacobi_apply(P, r):
     return z
 
 
+def coarse_v(S, t, block_of_node, conducting, group):
+    """Coarse space Z (n x nc, real), its Galerkin matrix E = Z^T S Z and E^-1.
+
+    Column c of Z is 1/t_d on the V dof d of every conducting node whose
+    subdomain id // group equals the c-th such group (in increasing order),
+    i.e. the unscaled field V = 1 on those nodes and 0 elsewhere.  The idea
+    follows the per-component gauge condition of Sec. 4 (V is fixed only up to
+    a constant on each conducting component); here the constants are taken
+    per group of subdomains of the partition (Sec. 3), which also captures
+    the smooth V modes along the conductor that block-Jacobi leaves slow."""
+    bon = np.asarray(block_of_node)
+    cond = np.asarray(conducting, dtype=bool)
+    nodes = np.nonzero(cond)[0]
+    n = S.shape[0]
+    if nodes.size == 0:
+        return None
+    grp = bon[nodes] // group
+    _, cid = np.unique(grp, return_inverse=True)
+    dofs = 4 * nodes + 3
+    Z = sp.csr_matrix((1.0 / np.asarray(t)[dofs], (dofs, cid)), shape=(n, int(cid.max()) + 1))
+    E = (Z.T @ (sp.csr_matrix(S) @ Z)).toarray()
+    return Z, E, np.linalg.inv(E)
+
+
+def two_level_apply(P, C, r):
+    """z = blockdiag(S_ss)^-1 r + Z E^-1 Z^T r (C = coarse_v(...), may be None)."""
+    z = block_jacobi_apply(P, r)
+    if C is not None:
+        Z, _, Ei = C
+        z = z + Z @ (Ei @ (Z.T @ r))
+    return z
+
+
 def givens(a, b):
     """Complex Givens rotation (c real, s complex) with [c s; -conj(s) c][a; b] = [r; 0]."""
     if b == 0.0:
@@ -67,19 +105,25 @@ def givens(a, b):
     return abs(a) / rho, ph * np.conj(b) / rho, ph * rho
 
 
-def cgs2(V, w):
+def cgs2(V, w, selective=False):
     """Orthogonalise w against the orthonormal columns of V twice (CGS2).
 
     Returns (h, w_new, beta) with h = coefficients accumulated over both
-    passes (Hermitian inner product) and beta = ||w_new||."""
+    passes (Hermitian inner product) and beta = ||w_new||.  With
+    selective=True the second pass runs only when the first one removed more
+    than half of ||w||^2 (||w_1||^2 < ||w_0||^2 / 2, the Daniel-Gragg-Kaufman-
+    Stewart test with eta = 1/sqrt(2))."""
+    n0 = np.vdot(w, w).real
     h1 = V.conj().T @ w
     w = w - V @ h1
+    if selective and np.vdot(w, w).real >= 0.5 * n0:
+        return h1, w, np.linalg.norm(w)
     h2 = V.conj().T @ w
     w = w - V @ h2
     return h1 + h2, w, np.linalg.norm(w)
 
 
-def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000):
+def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000, selective=False):
     """Restarted right-preconditioned flexible GMRES.
 
     A and precond are callables (or matrices).  Stops when the true residual
@@ -115,7 +159,7 @@ def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000):
         for j in range(m):
             Z[:, j] = pc(V[:, j])
             w = mv(Z[:, j])
-            h, w, hn = cgs2(V[:, :j + 1], w)
+            h, w, hn = cgs2(V[:, :j + 1], w, selective)
             H[:j + 1, j] = h
             H[j + 1, j] = hn
             for i in range(j):                      # previous rotations

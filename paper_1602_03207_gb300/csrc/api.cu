@@ -46,6 +46,7 @@ void ect_default_options(ect_options* o) {
     o->use_graph = 1;
     o->rhs_tile = 0;
     o->timeout_s = 0.0;
+    o->reorth = 1;
 }
 
 int ect_create(ect_ctx** out, void* stream) {
@@ -113,11 +114,11 @@ int ect_assemble(ect_ctx* c, int which, int precision_mask) {
     });
 }
 
-int ect_precond_setup(ect_ctx* c, int which, int precision_mask) {
+int ect_precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {
         workspace_free(c);
-        precond_setup(c, which, precision_mask);
+        precond_setup(c, which, precision_mask, coarse_group);
     });
 }
 
@@ -177,6 +178,7 @@ int ect_precond_apply(ect_ctx* c, int which, int precision, const void* d_r, voi
         ECT_REQUIRE(d_r && d_z && k >= 1 && k <= 65535, ECT_ERR_ARG, "bad precond arguments");
         ECT_REQUIRE(d_r != d_z, ECT_ERR_ARG, "r and z must not overlap");
         const int64_t ld = 4 * c->n_nodes;
+        coarse_scratch(c, which, k);
         if (precision == ECT_F64) precond_apply_f64(c, which, (const double2*)d_r, (double2*)d_z, k, ld, 0, nullptr);
         else if (precision == ECT_F32) precond_apply_f32(c, which, (const float2*)d_r, (float2*)d_z, k, ld, 0, nullptr);
         else throw EctError{ECT_ERR_ARG, "bad precision"};
@@ -203,6 +205,86 @@ int ect_solve(ect_ctx* c, int which, const void* d_rhs, void* d_x, int k, const 
         if (opt) o = *opt;
         else ect_default_options(&o);
         solve(c, which, (const double2*)d_rhs, (double2*)d_x, k, o, st);
+    });
+}
+
+int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, const ect_options* base,
+                 ect_options* best, ect_stats* stats) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] {
+        check_which(which);
+        ECT_REQUIRE(d_rhs && d_work && best && k >= 1, ECT_ERR_ARG, "bad autotune arguments");
+        ect_options o;
+        if (base) o = *base;
+        else ect_default_options(&o);
+        Matrix& M = c->mat[which];
+        ECT_REQUIRE(M.assembled && M.pc_f64, ECT_ERR_STATE, "assemble and set up the preconditioner first");
+        const bool mixed = o.mode == ECT_MODE_MIXED;
+        ECT_REQUIRE(!mixed || (M.has_f32 && M.pc_f32), ECT_ERR_STATE, "mixed mode needs the FP32 operators");
+        cudaStream_t st = c->stream;
+        const int64_t ld = 4 * c->n_nodes;
+        coarse_scratch(c, which, k);
+        // 1. kernel tile: SpMM + preconditioner apply on the solver's precision
+        DevBuf a, b;
+        const size_t esz = mixed ? sizeof(float2) : sizeof(double2);
+        a.alloc(esz * ld * k);
+        b.alloc(esz * ld * k);
+        ECT_CUDA(cudaMemsetAsync(a.p, 0, a.bytes, st));
+        int best_tile = 1;
+        float best_ms = 1e30f;
+        for (int kt : {1, 2, 4, 8}) {
+            if (kt > 1 && kt > 2 * k) break;
+            auto run = [&] {
+                if (mixed) {
+                    spmv_f32(c, which, a.as<float2>(), b.as<float2>(), k, ld, kt, nullptr);
+                    precond_apply_f32(c, which, b.as<float2>(), a.as<float2>(), k, ld, kt, nullptr);
+                } else {
+                    spmv_f64(c, which, true, a.as<double2>(), b.as<double2>(), k, ld, kt, nullptr);
+                    precond_apply_f64(c, which, b.as<double2>(), a.as<double2>(), k, ld, kt, nullptr);
+                }
+            };
+            run();
+            ECT_CUDA(cudaEventRecord(c->ev0, st));
+            for (int r = 0; r < 5; ++r) run();
+            ECT_CUDA(cudaEventRecord(c->ev1, st));
+            ECT_CUDA(cudaEventSynchronize(c->ev1));
+            float ms = 0.f;
+            ECT_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_tile = kt;
+            }
+        }
+        o.rhs_tile = best_tile;
+        // 2. Krylov lengths: full solves, fastest converged wins
+        std::vector<std::pair<int, int>> cand;
+        if (mixed) cand = {{6, 20}, {8, 30}, {10, 30}, {6, 50}, {4, 64}};
+        else cand = {{20, 0}, {30, 0}, {45, 0}, {64, 0}};
+        double best_t = 1e300;
+        ect_options win = o;
+        ect_stats wst{};
+        bool any = false;
+        for (auto& pr : cand) {
+            ect_options t = o;
+            t.restart = pr.first;
+            if (mixed) t.inner_iters = pr.second;
+            ect_stats s{};
+            try {
+                solve(c, which, (const double2*)d_rhs, (double2*)d_work, k, t, &s);
+            } catch (const EctError& e) {
+                if (e.code != ECT_ERR_NOT_CONVERGED && e.code != ECT_ERR_TIMEOUT) throw;
+                continue;
+            }
+            if (s.ms < best_t) {
+                best_t = s.ms;
+                win = t;
+                wst = s;
+                any = true;
+            }
+        }
+        ECT_REQUIRE(any, ECT_ERR_NOT_CONVERGED, "no autotune candidate converged");
+        *best = win;
+        if (stats) *stats = wst;
     });
 }
 

@@ -148,9 +148,25 @@ struct Matrix {
     DevBuf t;              // double[4N] scaling
     DevBuf pinv;           // double2 block inverses (column-major per block)
     DevBuf pinv32;         // float2  block inverses
+    // conductor-V coarse space (two-level preconditioner)
+    int64_t nc = 0;        // coarse unknowns (0 = one-level)
+    int coarse_group = 0;
+    DevBuf einv, einv32;   // E^-1 (nc x nc, symmetric), FP64 and FP32
+    DevBuf blk_c;          // int32[n_blocks] coarse index of each subdomain, -1 if none
+    DevBuf agg_lo, agg_hi; // int32[nc] node range of each coarse group
+    DevBuf zv, zv32;       // 1/t at the V dof of conducting nodes, 0 elsewhere (N)
+    DevBuf rc, zc;         // coarse scratch [k][nc] (double2 or float2 storage)
+    int64_t coarse_k = 0;
+    std::vector<uint8_t> h_cond;  // conducting-node flags (host)
     void reset() {
         assembled = has_f32 = pc_f64 = pc_f32 = false;
-        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &t, &pinv, &pinv32}) b->release();
+        nc = 0;
+        coarse_group = 0;
+        coarse_k = 0;
+        h_cond.clear();
+        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
+                          &agg_lo, &agg_hi, &zv, &zv32, &rc, &zc})
+            b->release();
     }
 };
 
@@ -183,6 +199,7 @@ struct ect_ctx {
     DevBuf omega_d;        // int32 list of defect tets
     int64_t n_omega_d = 0;
     std::vector<int32_t> h_block_ptr;
+    std::vector<int32_t> h_row_ptr, h_col;
     Matrix mat[2];
     Workspace* ws = nullptr;
     // scratch
@@ -205,7 +222,8 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
                 const double* sigma, const double* nu, const double* sigma_d, const double* nu_d,
                 const int32_t* block_of_node, const uint8_t* bc_mask);
 void assemble_matrix(ect_ctx* c, int which, int precision_mask);
-void precond_setup(ect_ctx* c, int which, int precision_mask);
+void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group);
+void coarse_scratch(ect_ctx* c, int which, int k);
 
 // y = A x for k vectors; A = unscaled F64 (scaled=false) or scaled S (scaled=true)
 void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, int k, int64_t ldx,

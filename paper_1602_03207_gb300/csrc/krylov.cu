@@ -73,11 +73,13 @@ __device__ __forceinline__ void chunk_range(int64_t n, int G, int g, int64_t& lo
 }
 
 // part[(r*nvec + i)*G + g] = sum over this CTA's range of conj(V_i[r][e]) * W[r][e]
+// and, when wpart is given, wpart[r*G + g] = sum of |W[r][e]|^2 over the range
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_mdot(const C<T>* __restrict__ V, int64_t vstride, int nvec,
                                               const C<T>* __restrict__ W, int64_t ld, int64_t n,
-                                              const int* __restrict__ live, double2* __restrict__ part, int G) {
-    __shared__ double sh[8 * 2 * GV];
+                                              const int* __restrict__ live, double2* __restrict__ part, int G,
+                                              double* __restrict__ wpart) {
+    __shared__ double sh[8 * (2 * GV + 1)];
     const int r = blockIdx.y, g = blockIdx.x;
     if (live && !live[r]) return;
     int64_t lo, hi;
@@ -85,26 +87,48 @@ __global__ void __launch_bounds__(TPB) k_mdot(const C<T>* __restrict__ V, int64_
     const C<T>* w = W + (int64_t)r * ld;
     for (int i0 = 0; i0 < nvec; i0 += GV) {
         C<T> acc[GV];
+        T wn = T(0);
 #pragma unroll
         for (int q = 0; q < GV; ++q) acc[q] = czero<T>();
         for (int64_t e = lo + threadIdx.x; e < hi; e += TPB) {
             const C<T> we = w[e];
+            wn += we.x * we.x + we.y * we.y;
 #pragma unroll
             for (int q = 0; q < GV; ++q)
                 if (i0 + q < nvec) cfma_conj(acc[q], V[(int64_t)(i0 + q) * vstride + (int64_t)r * ld + e], we);
         }
-        double s[2 * GV];
+        double s[2 * GV + 1];
 #pragma unroll
         for (int q = 0; q < GV; ++q) {
             s[2 * q] = (double)acc[q].x;
             s[2 * q + 1] = (double)acc[q].y;
         }
-        block_sum<2 * GV>(s, sh);
-        if (threadIdx.x == 0)
+        s[2 * GV] = (double)wn;
+        block_sum<2 * GV + 1>(s, sh);
+        if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = 0; q < GV; ++q)
                 if (i0 + q < nvec) part[((int64_t)r * nvec + i0 + q) * G + g] = make_double2(s[2 * q], s[2 * q + 1]);
+            if (wpart && i0 == 0) wpart[(int64_t)r * G + g] = s[2 * GV];
+        }
     }
+}
+
+// second Gram-Schmidt pass needed?  live2[r] = live[r] && ||w1||^2 < ||w0||^2 / 2
+__global__ void k_reorth_decide(const double* __restrict__ wpart, const double* __restrict__ npart, int G, int k,
+                                const int* __restrict__ live, int* __restrict__ live2) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= k) return;
+    if (!live[r]) {
+        live2[r] = 0;
+        return;
+    }
+    double n0 = 0.0, n1 = 0.0;
+    for (int g = 0; g < G; ++g) {
+        n0 += wpart[(int64_t)r * G + g];
+        n1 += npart[(int64_t)r * G + g];
+    }
+    live2[r] = (n1 < 0.5 * n0) ? 1 : 0;
 }
 
 // hp[r*ldp + i] = sum_g part; H[r*ldh + hoff + i] (+)= the same
@@ -393,8 +417,9 @@ struct Workspace {
     DevBuf V32, U32;
     DevBuf H, cs, sn, g, y, hp;
     DevBuf Hi, csi, sni, gi, yi;
-    DevBuf part, npart;
-    DevBuf bnorm, rnorm, target, target_i, inv_h, invb, run, live, live_i, nit, nit_i, flags;
+    DevBuf part, npart, wpart;
+    DevBuf bnorm, rnorm, target, target_i, inv_h, invb, run, live, live_i, nit, nit_i, flags, live2;
+    bool selective = true;
     std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
     ~Workspace() {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -454,6 +479,8 @@ Workspace* get_ws(ect_ctx* c, int k, int m, int mi, int mode) {
     }
     w->part.alloc(sizeof(double2) * (size_t)k * (mm + 1) * w->G);
     w->npart.alloc(sizeof(double) * (size_t)k * w->G);
+    w->wpart.alloc(sizeof(double) * (size_t)k * w->G);
+    w->live2.alloc(sizeof(int) * k);
     for (DevBuf* b : {&w->bnorm, &w->rnorm, &w->target, &w->target_i, &w->inv_h, &w->invb})
         b->alloc(sizeof(double) * k);
     for (DevBuf* b : {&w->run, &w->live, &w->live_i, &w->nit, &w->nit_i}) b->alloc(sizeof(int) * k);
@@ -481,12 +508,21 @@ void cgs2_step(ect_ctx* c, Workspace* w, const C<T>* V, int64_t vstride, int j, 
     const int ldp = std::max(w->m, w->mi) + 1;
     const int64_t ldh = (int64_t)(m + 1) * m, hoff = (int64_t)j * (m + 1);
     const unsigned rb = grid_for((int64_t)k * nvec * 32, 256);
-    for (int pass = 0; pass < 2; ++pass) {
-        k_mdot<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live, part, G);
-        k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live, hp, ldp, H, ldh, hoff, pass);
-        k_maxpy<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live,
-                                             pass == 1 ? w->npart.as<double>() : nullptr, G);
+    const bool sel = w->selective && live != nullptr;
+    double* npart = w->npart.as<double>();
+    // pass 1
+    k_mdot<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live, part, G, sel ? w->wpart.as<double>() : nullptr);
+    k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live, hp, ldp, H, ldh, hoff, 0);
+    k_maxpy<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live, sel ? npart : nullptr, G);
+    // pass 2 (for the right-hand sides that need it when selective)
+    const int* live2 = live;
+    if (sel) {
+        k_reorth_decide<<<grid_for(k, 128), 128, 0, st>>>(w->wpart.as<double>(), npart, G, k, live, w->live2.as<int>());
+        live2 = w->live2.as<int>();
     }
+    k_mdot<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live2, part, G, nullptr);
+    k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live2, hp, ldp, H, ldh, hoff, 1);
+    k_maxpy<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live2, npart, G);
     ECT_CHECK_LAUNCH();
 }
 
@@ -582,7 +618,13 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
     }
     cudaStream_t st = c->stream;
     ECT_CUDA(cudaEventRecord(c->ev0, st));
+    coarse_scratch(c, which, k);
     Workspace* w = get_ws(c, k, opt.restart, mi, opt.mode);
+    if (w->selective != (opt.reorth != 0)) {
+        for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
+        w->graphs.clear();
+        w->selective = opt.reorth != 0;
+    }
     const int64_t n = w->n, ld = n;
     const double* t = M.t.as<double>();
     // scaled right-hand side and its norms; Y = 0, R = Bh
@@ -704,6 +746,7 @@ void cgs2_entry(ect_ctx* c, int precision, const void* V, int j, int64_t n, void
     tmp.G = pick_G(n, 1);
     tmp.part.alloc(sizeof(double2) * (j + 1) * tmp.G);
     tmp.npart.alloc(sizeof(double) * tmp.G);
+    tmp.selective = false;
     tmp.hp.alloc(sizeof(double2) * (j + 1));
     DevBuf H, nrm;
     H.alloc(sizeof(double2) * (j + 1) * j);

@@ -177,10 +177,11 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
         }
         if (s1[t] != s0[t] || n1[t] != n0[t]) od.push_back((int32_t)t);
     }
-    std::vector<uint8_t> fm[2];
+    std::vector<uint8_t> fm[2], condv[2];
     for (int m = 0; m < 2; ++m) {
         const std::vector<double>& s = m ? s1 : s0;
-        std::vector<uint8_t> cond(n_nodes, 0);
+        std::vector<uint8_t>& cond = condv[m];
+        cond.assign(n_nodes, 0);
         for (int64_t t = 0; t < n_tets; ++t)
             if (s[t] > 0.0)
                 for (int a = 0; a < 4; ++a) cond[tets[4 * t + a]] = 1;
@@ -212,6 +213,7 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     ECT_CUDA(cudaMemcpyAsync(c->pinv_off.p, poff.data(), c->pinv_off.bytes, cudaMemcpyHostToDevice, st));
     for (int m = 0; m < 2; ++m) {
         Matrix& M = c->mat[m];
+        M.h_cond = condv[m];
         M.sigma.alloc(sizeof(double) * n_tets);
         M.nu.alloc(sizeof(double) * n_tets);
         M.fixmask.alloc(n_nodes);
@@ -290,6 +292,9 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
                                                        c->slot_ptr.as<int32_t>(), c->diag_slot.as<int32_t>(),
                                                        c->entries.as<uint32_t>());
     ECT_CHECK_LAUNCH();
+    c->h_row_ptr = hrp;
+    c->h_col.resize(nnzb);
+    ECT_CUDA(cudaMemcpyAsync(c->h_col.data(), c->col.p, sizeof(int32_t) * nnzb, cudaMemcpyDeviceToHost, st));
     ECT_CUDA(cudaStreamSynchronize(st));
     c->mesh_set = true;
 }

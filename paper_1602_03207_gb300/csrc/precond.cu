@@ -12,6 +12,8 @@
 // elimination with partial (row) pivoting; the inverse is stored
 // column-major so that the apply kernel's threads (one per row) read it
 // coalesced.  Apply: one CTA per subdomain and tile of right-hand sides.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -119,7 +121,9 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
                                                     const int64_t* __restrict__ pinv_off,
                                                     const C<T>* __restrict__ pinv, const C<T>* __restrict__ r,
                                                     C<T>* __restrict__ z, int k, int64_t ld,
-                                                    const int* __restrict__ active) {
+                                                    const int* __restrict__ active,
+                                                    const int32_t* __restrict__ blk_c, const C<T>* __restrict__ zc,
+                                                    int64_t nc, const T* __restrict__ zv) {
     __shared__ C<T> rs[KT][64];
     const int blk = blockIdx.x, tid = threadIdx.x;
     const int r0 = blockIdx.y * KT;
@@ -143,9 +147,142 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
 #pragma unroll
         for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[q][cc]);
     }
+    if (zc && (tid & 3) == 3) {
+        const int cc = blk_c[blk];
+        const T w = zv[n0 + (tid >> 2)];
+        if (cc >= 0 && w != T(0))
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                const C<T> v = zc[(int64_t)(r0 + q) * nc + cc];
+                acc[q].x += w * v.x;
+                acc[q].y += w * v.y;
+            }
+    }
 #pragma unroll
     for (int q = 0; q < KT; ++q)
         if (on[q]) z[(int64_t)(r0 + q) * ld + base + tid] = acc[q];
+}
+
+// coarse restriction: rc[r][c] = sum over the group's nodes of zv[i] * r[r][4i+3]
+template <typename T>
+__global__ void __launch_bounds__(128) k_coarse_restrict(const C<T>* __restrict__ r, int64_t ld,
+                                                         const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                                                         const T* __restrict__ zv, int64_t nc,
+                                                         const int* __restrict__ active, C<T>* __restrict__ rc) {
+    __shared__ double sh[4][2];
+    const int cc = blockIdx.x, rr = blockIdx.y;
+    if (active && !active[rr]) return;
+    double sx = 0.0, sy = 0.0;
+    for (int i = lo[cc] + threadIdx.x; i < hi[cc]; i += blockDim.x) {
+        const T w = zv[i];
+        const C<T> v = r[(int64_t)rr * ld + 4 * (int64_t)i + 3];
+        sx += (double)(w * v.x);
+        sy += (double)(w * v.y);
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5][0] = sx;
+        sh[threadIdx.x >> 5][1] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sh[w][0];
+            b += sh[w][1];
+        }
+        rc[(int64_t)rr * nc + cc] = from_d<T>(make_double2(a, b));
+    }
+}
+
+// zc[r][c] = sum_d Einv[d][c] rc[r][d]  (Einv symmetric, read coalesced along c)
+template <typename T, int KT>
+__global__ void __launch_bounds__(256) k_coarse_gemv(const C<T>* __restrict__ einv, int64_t nc,
+                                                     const C<T>* __restrict__ rc, int k,
+                                                     const int* __restrict__ active, C<T>* __restrict__ zc) {
+    __shared__ C<T> rs[KT][256];
+    const int64_t cc = blockIdx.x * 256ll + threadIdx.x;
+    const int r0 = blockIdx.y * KT;
+    bool on[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    C<T> acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
+    for (int64_t d0 = 0; d0 < nc; d0 += 256) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+            rs[q][threadIdx.x] = (on[q] && d0 + threadIdx.x < nc) ? rc[(int64_t)(r0 + q) * nc + d0 + threadIdx.x]
+                                                                  : czero<T>();
+        __syncthreads();
+        if (cc < nc) {
+            const int64_t dn = nc - d0 < 256 ? nc - d0 : 256;
+            for (int64_t d = 0; d < dn; ++d) {
+                const C<T> a = einv[(d0 + d) * nc + cc];
+#pragma unroll
+                for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[q][d]);
+            }
+        }
+    }
+    if (cc < nc)
+#pragma unroll
+        for (int q = 0; q < KT; ++q)
+            if (on[q]) zc[(int64_t)(r0 + q) * nc + cc] = acc[q];
+}
+
+// in-place Gauss-Jordan inversion of the dense coarse matrix, pivot k (no
+// pivoting: e^{i pi/4} E has a positive definite Hermitian part).  Step 1
+// saves row k (scaled by 1/a_kk) and column k; step 2 updates everything.
+__global__ void k_gj_save(double2* __restrict__ a, int64_t n, int64_t k, double2* __restrict__ rowk,
+                          double2* __restrict__ colk, int* __restrict__ bad) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double2 piv = a[k * n + k];
+    const double m = piv.x * piv.x + piv.y * piv.y;
+    if (!(m > 0.0)) {
+        if (j == 0) atomicExch(bad, 1);
+        return;
+    }
+    const double2 p = make_double2(piv.x / m, -piv.y / m);
+    rowk[j] = j == k ? p : cmul(a[k * n + j], p);
+    colk[j] = a[j * n + k];
+}
+
+__global__ void k_gj_update(double2* __restrict__ a, int64_t n, int64_t k, const double2* __restrict__ rowk,
+                            const double2* __restrict__ colk) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int64_t i = e / n, j = e - i * n;
+    const double2 p = rowk[k];
+    if (i == k) {
+        a[e] = rowk[j];
+    } else if (j == k) {
+        const double2 v = cmul(colk[i], p);
+        a[e] = make_double2(-v.x, -v.y);
+    } else {
+        a[e] = csub(a[e], cmul(colk[i], rowk[j]));
+    }
+}
+
+__global__ void k_gather_vv(const double2* __restrict__ val, int64_t nnzb, double2* __restrict__ vv) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < nnzb) vv[s] = val[16 * s + 15];
+}
+
+__global__ void k_make_zv(const double* __restrict__ t, const uint8_t* __restrict__ fixmask, int64_t N,
+                          double* __restrict__ zv, float* __restrict__ zv32) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double w = (fixmask[i] & 8) ? 0.0 : 1.0 / t[4 * i + 3];
+    zv[i] = w;
+    zv32[i] = (float)w;
+}
+
+__global__ void k_d2f_vec(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) b[e] = make_float2((float)a[e].x, (float)a[e].y);
 }
 
 int pick_ptile(int k, int rhs_tile) {
@@ -158,25 +295,128 @@ int pick_ptile(int k, int rhs_tile) {
 }
 
 template <typename T>
-void apply_impl(ect_ctx* c, const C<T>* pinv, const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile,
-                const int* active) {
+void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const T* zv, const C<T>* r, C<T>* z,
+                int k, int64_t ld, int rhs_tile, const int* active) {
     const int kt = pick_ptile(k, rhs_tile);
     dim3 grid((unsigned)c->n_blocks, (unsigned)((k + kt - 1) / kt));
     const int32_t* bp = c->block_ptr.as<int32_t>();
     const int64_t* po = c->pinv_off.as<int64_t>();
     cudaStream_t st = c->stream;
+    const int64_t nc = M.nc;
+    C<T>* zc = nullptr;
+    if (nc > 0) {
+        ECT_REQUIRE(M.coarse_k >= k, ECT_ERR_STATE, "coarse scratch too small (internal)");
+        C<T>* rc = M.rc.as<C<T>>();
+        zc = M.zc.as<C<T>>();
+        k_coarse_restrict<T><<<dim3((unsigned)nc, (unsigned)k), 128, 0, st>>>(r, ld, M.agg_lo.as<int32_t>(),
+                                                                               M.agg_hi.as<int32_t>(), zv, nc, active, rc);
+        dim3 g2(grid_for(nc, 256), (unsigned)((k + kt - 1) / kt));
+        switch (kt) {
+            case 8: k_coarse_gemv<T, 8><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
+            case 4: k_coarse_gemv<T, 4><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
+            case 2: k_coarse_gemv<T, 2><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
+            default: k_coarse_gemv<T, 1><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
+        }
+    }
+    const int32_t* bc = M.blk_c.as<int32_t>();
     switch (kt) {
-        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active); break;
-        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active); break;
-        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active); break;
-        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active); break;
+        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
+        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
+        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
+        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
     }
     ECT_CHECK_LAUNCH();
 }
 
+// conductor-V coarse space: groups of `group` consecutive subdomains that
+// contain a conducting node; E = Z^T S Z = sum of the unscaled V-V couplings
+// between the groups' conducting nodes (assembled on the host in a fixed
+// order), inverted on the device.
+void coarse_setup(ect_ctx* c, int which, int group) {
+    Matrix& M = c->mat[which];
+    cudaStream_t st = c->stream;
+    const int64_t N = c->n_nodes, nb = c->n_blocks;
+    M.nc = 0;
+    M.coarse_group = group;
+    M.coarse_k = 0;
+    for (DevBuf* b : {&M.einv, &M.einv32, &M.blk_c, &M.agg_lo, &M.agg_hi, &M.zv, &M.zv32, &M.rc, &M.zc}) b->release();
+    if (group <= 0) return;
+    const std::vector<int32_t>& bp = c->h_block_ptr;
+    std::vector<int32_t> blk_c(nb, -1), lo, hi;
+    std::vector<int32_t> node_c(N, -1);
+    int64_t nc = 0;
+    for (int64_t g0 = 0; g0 < nb; g0 += group) {
+        const int64_t g1 = std::min<int64_t>(nb, g0 + group);
+        bool any = false;
+        for (int64_t i = bp[g0]; i < bp[g1] && !any; ++i) any = M.h_cond[i] != 0;
+        if (!any) continue;
+        for (int64_t b = g0; b < g1; ++b) blk_c[b] = (int32_t)nc;
+        for (int64_t i = bp[g0]; i < bp[g1]; ++i)
+            if (M.h_cond[i]) node_c[i] = (int32_t)nc;
+        lo.push_back(bp[g0]);
+        hi.push_back(bp[g1]);
+        ++nc;
+    }
+    if (nc == 0) return;
+    ECT_REQUIRE(nc <= 16384, ECT_ERR_ARG, "coarse space too large: use a larger coarse group");
+    // V-V couplings of the unscaled matrix
+    DevBuf vv;
+    vv.alloc(sizeof(double2) * c->nnzb);
+    k_gather_vv<<<grid_for(c->nnzb, 256), 256, 0, st>>>(M.val.as<double2>(), c->nnzb, vv.as<double2>());
+    ECT_CHECK_LAUNCH();
+    std::vector<double2> hvv(c->nnzb);
+    ECT_CUDA(cudaMemcpyAsync(hvv.data(), vv.p, vv.bytes, cudaMemcpyDeviceToHost, st));
+    ECT_CUDA(cudaStreamSynchronize(st));
+    std::vector<double2> E((size_t)nc * nc, make_double2(0.0, 0.0));
+    for (int64_t i = 0; i < N; ++i) {
+        const int ci = node_c[i];
+        if (ci < 0) continue;
+        for (int32_t s = c->h_row_ptr[i]; s < c->h_row_ptr[i + 1]; ++s) {
+            const int cj = node_c[c->h_col[s]];
+            if (cj < 0) continue;
+            double2& e = E[(size_t)ci * nc + cj];
+            e.x += hvv[s].x;
+            e.y += hvv[s].y;
+        }
+    }
+    M.einv.alloc(sizeof(double2) * nc * nc);
+    ECT_CUDA(cudaMemcpyAsync(M.einv.p, E.data(), M.einv.bytes, cudaMemcpyHostToDevice, st));
+    DevBuf rowk, colk, flag;
+    rowk.alloc(sizeof(double2) * nc);
+    colk.alloc(sizeof(double2) * nc);
+    flag.alloc(sizeof(int));
+    ECT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    for (int64_t kk = 0; kk < nc; ++kk) {
+        k_gj_save<<<grid_for(nc, 256), 256, 0, st>>>(M.einv.as<double2>(), nc, kk, rowk.as<double2>(),
+                                                     colk.as<double2>(), flag.as<int>());
+        k_gj_update<<<grid_for(nc * nc, 256), 256, 0, st>>>(M.einv.as<double2>(), nc, kk, rowk.as<double2>(),
+                                                            colk.as<double2>());
+    }
+    ECT_CHECK_LAUNCH();
+    int bad = 0;
+    ECT_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ECT_CUDA(cudaStreamSynchronize(st));
+    ECT_REQUIRE(!bad, ECT_ERR_BREAKDOWN, "the coarse matrix has a zero pivot");
+    M.einv32.alloc(sizeof(float2) * nc * nc);
+    k_d2f_vec<<<grid_for(nc * nc, 256), 256, 0, st>>>(M.einv.as<double2>(), M.einv32.as<float2>(), nc * nc);
+    M.blk_c.alloc(sizeof(int32_t) * nb);
+    M.agg_lo.alloc(sizeof(int32_t) * nc);
+    M.agg_hi.alloc(sizeof(int32_t) * nc);
+    ECT_CUDA(cudaMemcpyAsync(M.blk_c.p, blk_c.data(), M.blk_c.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(M.agg_lo.p, lo.data(), M.agg_lo.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(M.agg_hi.p, hi.data(), M.agg_hi.bytes, cudaMemcpyHostToDevice, st));
+    M.zv.alloc(sizeof(double) * N);
+    M.zv32.alloc(sizeof(float) * N);
+    k_make_zv<<<grid_for(N, 256), 256, 0, st>>>(M.t.as<double>(), M.fixmask.as<uint8_t>(), N, M.zv.as<double>(),
+                                                M.zv32.as<float>());
+    ECT_CHECK_LAUNCH();
+    ECT_CUDA(cudaStreamSynchronize(st));
+    M.nc = nc;
+}
+
 }  // namespace
 
-void precond_setup(ect_ctx* c, int which, int precision_mask) {
+void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) {
     ECT_REQUIRE(which == ECT_VACUUM || which == ECT_DEFECT, ECT_ERR_ARG, "bad which");
     Matrix& M = c->mat[which];
     ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "ect_assemble must come before ect_precond_setup");
@@ -199,20 +439,50 @@ void precond_setup(ect_ctx* c, int which, int precision_mask) {
     ECT_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     ECT_CUDA(cudaStreamSynchronize(st));
     ECT_REQUIRE(!h, ECT_ERR_BREAKDOWN, "a subdomain block of the scaled matrix is singular");
+    if (coarse_group < 0) {
+        // automatic: the smallest power-of-two group with at most 3072 coarse unknowns
+        int g = 1;
+        for (; g < (1 << 20); g *= 2) {
+            int64_t cnt = 0;
+            const std::vector<int32_t>& bp = c->h_block_ptr;
+            for (int64_t g0 = 0; g0 < c->n_blocks; g0 += g) {
+                const int64_t g1 = std::min<int64_t>(c->n_blocks, g0 + g);
+                for (int64_t i = bp[g0]; i < bp[g1]; ++i)
+                    if (M.h_cond[i]) {
+                        ++cnt;
+                        break;
+                    }
+            }
+            if (cnt <= 3072) break;
+        }
+        coarse_group = g;
+    }
+    coarse_setup(c, which, coarse_group);
     M.pc_f64 = true;
     M.pc_f32 = f32;
+}
+
+void coarse_scratch(ect_ctx* c, int which, int k) {
+    Matrix& M = c->mat[which];
+    if (M.nc == 0 || M.coarse_k >= k) return;
+    workspace_free(c);  // captured graphs hold the old scratch pointers
+    M.rc.alloc(sizeof(double2) * M.nc * k);
+    M.zc.alloc(sizeof(double2) * M.nc * k);
+    M.coarse_k = k;
 }
 
 void precond_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld, int rhs_tile,
                        const int* active) {
     Matrix& M = c->mat[which];
     ECT_REQUIRE(M.pc_f64, ECT_ERR_STATE, "preconditioner not set up");
-    apply_impl<double>(c, M.pinv.as<double2>(), r, z, k, ld, rhs_tile, active);
+    apply_impl<double>(c, M, M.pinv.as<double2>(), M.einv.as<double2>(), M.zv.as<double>(), r, z, k, ld, rhs_tile,
+                       active);
 }
 
 void precond_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld, int rhs_tile,
                        const int* active) {
     Matrix& M = c->mat[which];
     ECT_REQUIRE(M.pc_f32, ECT_ERR_STATE, "FP32 preconditioner not set up (use ECT_F32 in ect_precond_setup)");
-    apply_impl<float>(c, M.pinv32.as<float2>(), r, z, k, ld, rhs_tile, active);
+    apply_impl<float>(c, M, M.pinv32.as<float2>(), M.einv32.as<float2>(), M.zv32.as<float>(), r, z, k, ld, rhs_tile,
+                      active);
 }

@@ -33,7 +33,7 @@ _NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_CUDA", 4: "ERR_OOM", 5: 
 EXPORTS = ["ect_default_options", "ect_create", "ect_destroy", "ect_last_error", "ect_set_mesh",
            "ect_set_physics", "ect_assemble", "ect_precond_setup", "ect_matrix_info", "ect_matrix_copy",
            "ect_scaling_copy", "ect_spmv", "ect_precond_apply", "ect_cgs2", "ect_coil_rhs", "ect_solve",
-           "ect_delta_z", "ect_impedance"]
+           "ect_delta_z", "ect_impedance", "ect_autotune"]
 
 
 class EctError(RuntimeError):
@@ -51,7 +51,7 @@ class Coil(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("mode", ctypes.c_int), ("inner_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("rhs_tile", ctypes.c_int), ("timeout_s", ctypes.c_double)]
+                ("rhs_tile", ctypes.c_int), ("timeout_s", ctypes.c_double), ("reorth", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -83,7 +83,7 @@ def load_library(path=LIB_PATH):
         "ect_set_mesh": (I, [P, P, I64, P, I64, P, P, P, P, P, P]),
         "ect_set_physics": (I, [P, D, D, D]),
         "ect_assemble": (I, [P, I, I]),
-        "ect_precond_setup": (I, [P, I, I]),
+        "ect_precond_setup": (I, [P, I, I, I]),
         "ect_matrix_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "ect_matrix_copy": (I, [P, I, P, P, P]),
         "ect_scaling_copy": (I, [P, I, P]),
@@ -93,6 +93,7 @@ def load_library(path=LIB_PATH):
         "ect_coil_rhs": (I, [P, ctypes.POINTER(Coil), P, I, P]),
         "ect_solve": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
         "ect_delta_z": (I, [P, P, P, P, P, P, P]),
+        "ect_autotune": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
         "ect_impedance": (I, [P, ctypes.POINTER(Coil), P, I, ctypes.POINTER(Options), P, ctypes.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
@@ -201,8 +202,8 @@ class Context:
     def assemble(self, which, precision_mask=ECT_F64):
         self._call(self.L.ect_assemble, int(which), int(precision_mask))
 
-    def precond_setup(self, which, precision_mask=ECT_F64):
-        self._call(self.L.ect_precond_setup, int(which), int(precision_mask))
+    def precond_setup(self, which, precision_mask=ECT_F64, coarse_group=-1):
+        self._call(self.L.ect_precond_setup, int(which), int(precision_mask), int(coarse_group))
 
     def matrix_info(self):
         n, nb = ctypes.c_int64(), ctypes.c_int64()
@@ -254,6 +255,15 @@ class Context:
             e.stats = st.as_dict()
             raise
         return st.as_dict()
+
+    def autotune(self, which, rhs, work, k, base=None):
+        """Pick rhs_tile, restart and inner_iters for this workload; returns (options, stats)."""
+        o = base if base is not None else default_options()
+        best = Options()
+        st = Stats()
+        self._call(self.L.ect_autotune, int(which), _dptr(rhs), _dptr(work), int(k), ctypes.byref(o),
+                   ctypes.byref(best), ctypes.byref(st))
+        return best, st.as_dict()
 
     def delta_z(self, u0, ud, b, currents):
         cur = np.ascontiguousarray(currents, dtype=np.float64)

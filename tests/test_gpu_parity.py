@@ -41,13 +41,13 @@ def small_problem(seed=1):
     return E.wall_loss_problem((10, 11, 13), (20e-3, 20e-3, 30e-3), (2, 3, 2), 0.15, seed, z_pos=(0.0,))
 
 
-def make_ctx(ect, p, f32=True):
+def make_ctx(ect, p, f32=True, group=1):
     ctx = ect.Context()
     ctx.load_problem(p)
     mask = ect.ECT_F64 | (ect.ECT_F32 if f32 else 0)
     for w in (ect.ECT_VACUUM, ect.ECT_DEFECT):
         ctx.assemble(w, mask)
-        ctx.precond_setup(w, mask)
+        ctx.precond_setup(w, mask, group)
     return ctx
 
 
@@ -130,13 +130,19 @@ def test_spmv_f32_scaled(ect, small):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_precond_apply(ect, small, prec):
-    p, ctx, M = small
+@pytest.mark.parametrize("group", [0, 1, 3])
+def test_precond_apply(ect, small, prec, group):
+    """Block-Jacobi (group 0) and the two-level conductor-V coarse space (groups 1, 3)."""
+    p, ctx1, M = small
+    ctx = ctx1 if group == 1 else make_ctx(ect, p, group=group)
     rng = np.random.default_rng(2)
     n = 4 * p.mesh.n_nodes
     t = fem.scaling(M["defect"])
     S = fem.scaled(M["defect"], t)
     P = solve.block_jacobi(S, p.mesh.block_of_node)
+    s, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, "defect")
+    cond = fem.conducting_nodes(p.mesh.n_nodes, p.mesh.tets, s)
+    C = solve.coarse_v(S, t, p.mesh.block_of_node, cond, group) if group else None
     R = crand(rng, 3, n)
     dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-9) if prec == "f64" else (torch.complex64, ect.ECT_F32, 1e-3))
     r = dev(R, dt)
@@ -144,7 +150,7 @@ def test_precond_apply(ect, small, prec):
     ctx.precond_apply(WHICH["defect"], r, z, 3, precision=pr)
     Z = z.cpu().numpy()
     for q in range(3):
-        ref = solve.block_jacobi_apply(P, R[q])
+        ref = solve.two_level_apply(P, C, R[q])
         assert np.linalg.norm(Z[q] - ref) <= tol * np.linalg.norm(ref)
 
 
@@ -301,3 +307,18 @@ def test_bad_meshes_rejected(ect):
         b = torch.zeros(1, 4 * m.n_nodes, dtype=torch.complex128, device="cuda")
         ctx.solve(0, b, torch.empty_like(b), 1)
     assert e.value.code == ect.ECT_ERR_STATE
+
+
+def test_autotune_returns_converging_options(ect, small):
+    p, ctx, M = small
+    n = 4 * p.mesh.n_nodes
+    B = np.stack([fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, c.as_tuple(), 0.0), p, "defect")
+                  for c in p.coils])
+    b = dev(B)
+    work = torch.empty_like(b)
+    for mode in (ect.ECT_MODE_F64, ect.ECT_MODE_MIXED):
+        best, st = ctx.autotune(1, b, work, 2, ect.default_options(tol=1e-10, mode=mode))
+        assert best.rhs_tile in (1, 2, 4, 8) and st["converged"] == 2
+        assert best.mode == mode and 1 <= best.restart <= 64
+        X, st2 = _solve_check(ect, p, ctx, M, "defect", best)
+        assert st2["converged"] == 2

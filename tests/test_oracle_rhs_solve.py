@@ -217,3 +217,76 @@ def test_signal_modes_as_printed():
     dz = np.array([[1 + 2j, 3 - 1j], [3 - 1j, -2 + 0.5j]])
     fa, f3 = impedance.signal_modes(dz)
     assert fa == 0.5j * (4 + 1j) and f3 == 0.5j * (3 + 1.5j)
+
+
+# ---------------------------------------------------------------- conductor-V coarse space
+
+def test_coarse_matrix_is_sum_of_unscaled_vv_couplings():
+    """E_cd = sum over conducting nodes i in group c, j in group d of M[V_i, V_j] (brute force)."""
+    p = tiny_problem((6, 6, 8), seed=4)
+    M = fem.system_matrix(p, "defect")
+    t = fem.scaling(M)
+    S = fem.scaled(M, t)
+    s, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, "defect")
+    cond = fem.conducting_nodes(p.mesh.n_nodes, p.mesh.tets, s)
+    Z, E, Ei = solve.coarse_v(S, t, p.mesh.block_of_node, cond, 2)
+    groups = sorted({int(b) // 2 for b in p.mesh.block_of_node[cond]})
+    Md = M.toarray()
+    ref = np.zeros((len(groups), len(groups)), dtype=complex)
+    for i in np.nonzero(cond)[0]:
+        for j in np.nonzero(cond)[0]:
+            ci = groups.index(int(p.mesh.block_of_node[i]) // 2)
+            cj = groups.index(int(p.mesh.block_of_node[j]) // 2)
+            ref[ci, cj] += Md[4 * i + 3, 4 * j + 3]
+    assert np.abs(E - ref).max() <= 1e-12 * np.abs(ref).max()
+    np.testing.assert_allclose(Ei @ E, np.eye(len(groups)), atol=1e-9)
+
+
+def test_coarse_correction_is_exact_on_the_coarse_space():
+    p = tiny_problem((6, 6, 8), seed=5)
+    M = fem.system_matrix(p, "vacuum")
+    t = fem.scaling(M)
+    S = fem.scaled(M, t)
+    s, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, "vacuum")
+    cond = fem.conducting_nodes(p.mesh.n_nodes, p.mesh.tets, s)
+    Z, E, Ei = solve.coarse_v(S, t, p.mesh.block_of_node, cond, 1)
+    c = np.random.default_rng(0).normal(size=Z.shape[1]) + 0j
+    r = S @ (Z @ c)
+    np.testing.assert_allclose(Z @ (Ei @ (Z.T @ r)), Z @ c, atol=1e-9 * np.abs(Z @ c).max())
+
+
+def test_two_level_removes_restart_stagnation():
+    """One-level FGMRES(30) stalls near 1e-7 on this mesh; the coarse V space converges."""
+    p = E.wall_loss_problem((9, 9, 12), (20e-3, 20e-3, 30e-3), (2, 2, 3), 0.1, 3, z_pos=(0.0,))
+    M = fem.system_matrix(p, "vacuum")
+    t = fem.scaling(M)
+    S = fem.scaled(M, t)
+    P = solve.block_jacobi(S, p.mesh.block_of_node)
+    cond = fem.conducting_nodes(p.mesh.n_nodes, p.mesh.tets, p.sigma)
+    C = solve.coarse_v(S, t, p.mesh.block_of_node, cond, 1)
+    b = fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, p.coils[0].as_tuple(), 0.0), p, "vacuum")
+    _, i1 = solve.fgmres(S, t * b, lambda r: solve.block_jacobi_apply(P, r), tol=1e-10, restart=30, maxiter=1500)
+    _, i2 = solve.fgmres(S, t * b, lambda r: solve.two_level_apply(P, C, r), tol=1e-10, restart=30, maxiter=1500)
+    assert i1["relres"] > 1e-9
+    assert i2["relres"] <= 1e-10 and i2["iters"] < 400
+
+
+def test_selective_reorthogonalisation():
+    rng = np.random.default_rng(8)
+    n, k = 300, 6
+    V, _ = np.linalg.qr(rng.normal(size=(n, k)) + 1j * rng.normal(size=(n, k)))
+    w = rng.normal(size=n) + 1j * rng.normal(size=n)          # mostly outside span(V): one pass
+    h, w2, _ = solve.cgs2(V, w, selective=True)
+    np.testing.assert_allclose(h, V.conj().T @ w, rtol=1e-13)
+    w = V @ (rng.normal(size=k) + 0j) + 1e-6 * (rng.normal(size=n) + 0j)   # nearly inside: two passes
+    h, w2, beta = solve.cgs2(V, w, selective=True)
+    assert np.abs(V.conj().T @ w2).max() < 1e-13 * np.linalg.norm(w)
+    p = tiny_problem()
+    M = fem.system_matrix(p, "defect")
+    t = fem.scaling(M)
+    S = fem.scaled(M, t)
+    P = solve.block_jacobi(S, p.mesh.block_of_node)
+    b = fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, p.coils[0].as_tuple(), 0.0), p, "defect")
+    y, info = solve.fgmres(S, t * b, lambda r: solve.block_jacobi_apply(P, r), tol=1e-11, restart=300,
+                           selective=True)
+    assert info["relres"] <= 1e-11

@@ -118,6 +118,12 @@ int ect_set_mesh(ect_ctx* ctx, const double* h_xyz, int64_t n_nodes,
                  const double* h_sigma_d, const double* h_nu_d,
                  const int32_t* h_block_of_node, const uint8_t* h_bc_mask);
 
+/* Replace the defect configuration (h_sigma_d, h_nu_d as in ect_set_mesh;
+ * NaN = background, NULL = no defect) on the current mesh without rebuilding
+ * the pattern: the defect matrix and its preconditioner must be assembled
+ * and set up again.  Used to scan many deposits on one mesh. */
+int ect_set_defect(ect_ctx* ctx, const double* h_sigma_d, const double* h_nu_d);
+
 /* Frequency (Hz), nu_tilde = 1/mu_tilde of the Coulomb-gauge penalty (Eq. CGCdiv
  * text) and the V-gauge penalty factor delta of Sec. 4 (1/m^2). */
 int ect_set_physics(ect_ctx* ctx, double freq_hz, double nu_tilde, double delta_gauge);
@@ -138,9 +144,14 @@ int ect_assemble(ect_ctx* ctx, int which, int precision_mask);
  * one coarse unknown per group of coarse_group consecutive subdomains that
  * contains a conducting node, V = 1 on that group's conducting nodes (after
  * the per-component gauge freedom of V noted in Sec. 4); its Galerkin matrix
- * is inverted densely.  0 = block-Jacobi only; < 0 = automatic group (the
- * smallest power of two giving at most 3072 coarse unknowns).  Coarse spaces
- * above 16384 unknowns are rejected with ECT_ERR_ARG. */
+ * is inverted densely (coarse spaces above 16384 unknowns are rejected with
+ * ECT_ERR_ARG).  0 = block-Jacobi only.  -1 = aggregation multigrid: the
+ * subdomains are the smoothing blocks and the aggregates of the first
+ * coarsening (4 coarse unknowns each, Galerkin coarse operators built from
+ * the constant field per component), deeper levels aggregate greedily up to
+ * 8 nodes, the coarsest level (<= 2048 unknowns) is inverted densely, and each
+ * application is one W-cycle with one block-Jacobi sweep before and after the
+ * coarse corrections. */
 int ect_precond_setup(ect_ctx* ctx, int which, int precision_mask, int coarse_group);
 
 /* Sizes of the assembled pattern: rows = n_nodes block rows, nnzb blocks. */
@@ -212,6 +223,32 @@ int ect_delta_z(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_
 int ect_impedance(ect_ctx* ctx, const ect_coil coils[2], const double* h_z_pos, int n_pos,
                   const ect_options* opt, double* h_dz, ect_stats* stats);
 
+/* ---- surrogate MLP ----------------------------------------------------------
+ * Not in the paper: a learned map from deposit parameters to the Delta Z
+ * signal along the probe path, trained on solver output.  Architecture
+ * 6 -> 256 -> 256 -> 256 -> 256 -> 256, SiLU hidden activations, linear
+ * output; bf16 weights and activations on tcgen05 tensor cores with fp32
+ * accumulation; fp32 master weights and Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8); loss L = 1/(2 B D) sum (y - t)^2.
+ * Parameters (float, ect_mlp_num_params() of them): for each layer in order,
+ * W (out x in, row-major) then b (out).
+ * x: float [batch][6], y/t: float [batch][256], device pointers. */
+typedef struct ect_mlp ect_mlp;
+int ect_mlp_num_params(void);
+/* batch: multiple of 128 (of 256 above 256). */
+int ect_mlp_create(ect_mlp** out, void* cuda_stream, int batch);
+void ect_mlp_destroy(ect_mlp* m);
+const char* ect_mlp_last_error(const ect_mlp* m);
+/* Set the fp32 parameters (host) and reset the Adam state. */
+int ect_mlp_set_params(ect_mlp* m, const float* h_params);
+int ect_mlp_get_params(ect_mlp* m, float* h_params);
+/* y = MLP(x) for one batch. */
+int ect_mlp_forward(ect_mlp* m, const float* d_x, float* d_y);
+/* Loss and its gradient with respect to every parameter (host, same layout). */
+int ect_mlp_gradients(ect_mlp* m, const float* d_x, const float* d_t, float* h_grads, double* h_loss);
+/* One Adam step on the batch (x, t); *h_loss (if not NULL) receives the loss
+ * before the step, which synchronises the stream. */
+int ect_mlp_train_step(ect_mlp* m, const float* d_x, const float* d_t, float lr, double* h_loss);
 
 #ifdef __cplusplus
 }

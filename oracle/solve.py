@@ -182,3 +182,114 @@ def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000, se
         r = b - mv(x)
         beta = np.linalg.norm(r)
     return x, dict(iters=total, relres=beta / bnorm, history=hist)
+
+
+# ---------------------------------------------------------------- aggregation multigrid
+#
+# Multilevel version of the subdomain idea: the subdomains of the partition
+# (Sec. 3, Step 2) are the aggregates of the first coarsening, and they are
+# also the smoothing blocks of the finest level.  Definitions:
+#   * near-null weights w: 1/t on free dofs of the finest level (the unscaled
+#     field equal to 1 in one component), 0 on constrained dofs; on coarser
+#     levels 1 on non-empty coarse dofs, 0 on empty ones;
+#   * tentative prolongator P (no smoothing): column (I, c) holds w on the
+#     component-c dofs of the nodes of aggregate I; E = P^T A P, plus the
+#     identity on coarse dofs whose column is empty;
+#   * coarse node graph: I ~ J when some node of I shares a stored block with
+#     some node of J (the finest graph is "nodes share a tet");
+#   * aggregates of a coarse level: greedy in increasing node order, a seed
+#     takes its not yet aggregated neighbours (increasing order) up to
+#     `agg_size` nodes; coarse nodes are renumbered so that aggregates are
+#     contiguous (stable by aggregate);
+#   * cycle: z = B^-1 r; gamma times { z += P mg(P^T (r - A z)) }; z += B^-1 (r - A z),
+#     with B the block diagonal over the level's aggregates, gamma = 2 (W-cycle)
+#     and 1 when the next level is the coarsest, which is solved densely.
+
+
+def node_graph_from_tets(n_nodes, tets):
+    tets = np.asarray(tets, dtype=np.int64)
+    r = np.repeat(tets, 4, axis=1).ravel()
+    c = np.tile(tets, (1, 4)).ravel()
+    G = sp.csr_matrix((np.ones(r.size, dtype=np.int8), (r, c)), shape=(n_nodes, n_nodes))
+    G.sum_duplicates()
+    G.sort_indices()
+    return G
+
+
+def greedy_aggregates(G, agg_size):
+    G = sp.csr_matrix(G)
+    G.sort_indices()
+    n = G.shape[0]
+    agg = -np.ones(n, dtype=np.int64)
+    na = 0
+    for i in range(n):
+        if agg[i] >= 0:
+            continue
+        members = [i]
+        for j in G.indices[G.indptr[i]:G.indptr[i + 1]]:
+            if len(members) >= agg_size:
+                break
+            if j != i and agg[j] < 0:
+                members.append(j)
+        agg[members] = na
+        na += 1
+    return agg
+
+
+def amg_setup(S, w0, node_agg0, G0, max_coarse_dofs=2048, agg_size=8):
+    """Levels of the aggregation hierarchy (see the notes above).
+
+    S: scaled matrix, w0: finest near-null weights (4n), node_agg0: aggregate of
+    each finest node (non-decreasing, the subdomain blocks), G0: finest node graph."""
+    levels = []
+    A = sp.csr_matrix(S)
+    w = np.asarray(w0, dtype=np.float64)
+    agg = np.asarray(node_agg0, dtype=np.int64)
+    G = sp.csr_matrix(G0)
+    while True:
+        n = A.shape[0] // 4
+        na = int(agg.max()) + 1
+        BJ = block_jacobi(A, agg)
+        rows = np.arange(4 * n)
+        cols = 4 * np.repeat(agg, 4) + np.tile(np.arange(4), n)
+        P = sp.csr_matrix((w, (rows, cols)), shape=(4 * n, 4 * na))
+        empty = np.asarray(abs(P).sum(axis=0)).ravel() == 0
+        Ac = (P.T @ A @ P).tocsr() + sp.diags(empty.astype(np.float64))
+        wc = np.where(empty, 0.0, 1.0)
+        Ag = sp.csr_matrix((np.ones(n, dtype=np.int8), (agg, np.arange(n))), shape=(na, n))
+        Gc = (Ag @ G @ Ag.T).tocsr()
+        Gc.sort_indices()
+        if 4 * na <= max_coarse_dofs:
+            levels.append(dict(A=A, P=P, BJ=BJ))
+            Acd = Ac.toarray()
+            levels.append(dict(A=Ac, inv=np.linalg.inv(Acd)))
+            return levels
+        cagg = greedy_aggregates(Gc, agg_size)
+        order = np.argsort(cagg, kind="stable")
+        perm = (4 * order[:, None] + np.arange(4)[None]).ravel()
+        P = P[:, perm].tocsr()
+        levels.append(dict(A=A, P=P, BJ=BJ))
+        A = Ac[perm][:, perm].tocsr()
+        w = wc[perm]
+        G = Gc[order][:, order].tocsr()
+        G.sort_indices()
+        agg = cagg[order]
+
+
+def amg_apply(levels, r, l=0, gamma=2):
+    L = levels[l]
+    if "inv" in L:
+        return L["inv"] @ r
+    A, P, BJ = L["A"], L["P"], L["BJ"]
+    z = block_jacobi_apply(BJ, r)
+    g = 1 if "inv" in levels[l + 1] else gamma
+    for _ in range(g):
+        z = z + P @ amg_apply(levels, P.T @ (r - A @ z), l + 1, gamma)
+    z = z + block_jacobi_apply(BJ, r - A @ z)
+    return z
+
+
+def near_null_weights(t, fixed_dofs):
+    w = 1.0 / np.asarray(t, dtype=np.float64)
+    w[np.asarray(fixed_dofs)] = 0.0
+    return w

@@ -90,6 +90,11 @@ int ect_set_mesh(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* 
     });
 }
 
+int ect_set_defect(ect_ctx* c, const double* sigma_d, const double* nu_d) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] { set_defect(c, sigma_d, nu_d); });
+}
+
 int ect_set_physics(ect_ctx* c, double freq, double nu_tilde, double delta) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {

@@ -136,6 +136,10 @@ struct DevBuf {
 // ----------------------------------------------------------------------------
 // context
 // ----------------------------------------------------------------------------
+struct Multigrid;  // aggregation multigrid hierarchy (multigrid.cu)
+struct Matrix;
+void mg_free(Matrix& M);
+
 struct Matrix {
     bool assembled = false;
     bool has_f32 = false;
@@ -158,7 +162,13 @@ struct Matrix {
     DevBuf rc, zc;         // coarse scratch [k][nc] (double2 or float2 storage)
     int64_t coarse_k = 0;
     std::vector<uint8_t> h_cond;  // conducting-node flags (host)
+    Multigrid* mg = nullptr;
+    Matrix() = default;
+    Matrix(const Matrix&) = delete;
+    Matrix& operator=(const Matrix&) = delete;
+    ~Matrix() { mg_free(*this); }
     void reset() {
+        mg_free(*this);
         assembled = has_f32 = pc_f64 = pc_f32 = false;
         nc = 0;
         coarse_group = 0;
@@ -200,6 +210,9 @@ struct ect_ctx {
     int64_t n_omega_d = 0;
     std::vector<int32_t> h_block_ptr;
     std::vector<int32_t> h_row_ptr, h_col;
+    std::vector<int32_t> h_tets;
+    std::vector<uint8_t> h_bc;
+    std::vector<double> h_sigma0, h_nu0;
     Matrix mat[2];
     Workspace* ws = nullptr;
     // scratch
@@ -221,9 +234,16 @@ inline double* ctx_scratch(ect_ctx* c, size_t doubles) {
 void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                 const double* sigma, const double* nu, const double* sigma_d, const double* nu_d,
                 const int32_t* block_of_node, const uint8_t* bc_mask);
+void set_defect(ect_ctx* c, const double* sigma_d, const double* nu_d);
 void assemble_matrix(ect_ctx* c, int which, int precision_mask);
 void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group);
 void coarse_scratch(ect_ctx* c, int which, int k);
+void mg_setup(ect_ctx* c, int which, bool f32);
+void mg_scratch(Matrix& M, int k);
+void mg_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld, int tile, const int* active);
+void mg_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld, int tile, const int* active);
+int mg_levels(const Matrix& M);
+bool mg_ready(const Matrix& M, int k);
 
 // y = A x for k vectors; A = unscaled F64 (scaled=false) or scaled S (scaled=true)
 void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, int k, int64_t ldx,
@@ -234,6 +254,22 @@ void precond_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int 
                        int rhs_tile, const int* active);
 void precond_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld,
                        int rhs_tile, const int* active);
+// generic building blocks (spmv.cu, precond.cu) shared by the multigrid levels
+void bsr_spmv_f64(cudaStream_t st, const int32_t* rp, const int32_t* cl, const double2* val, int64_t N,
+                  const double2* x, const double2* b, double2* y, int k, int64_t ldx, int rhs_tile, const int* active);
+void bsr_spmv_f32(cudaStream_t st, const int32_t* rp, const int32_t* cl, const float2* val, int64_t N,
+                  const float2* x, const float2* b, float2* y, int k, int64_t ldx, int rhs_tile, const int* active);
+void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, const double2* sval, const int32_t* bptr,
+                    const int64_t* poff, int64_t n_blocks, int max_block_nodes, double2* pinv, float2* pinv32);
+template <typename T>
+void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, const C<T>* pinv, int64_t n_blocks,
+                 const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate);
+void dense_inverse(cudaStream_t st, double2* a, int64_t n);
+void to_f32(cudaStream_t st, const double2* a, float2* b, int64_t n);
+template <typename T>
+void dense_gemv(cudaStream_t st, const C<T>* einv, int64_t nc, const C<T>* r, C<T>* z, int k, int rhs_tile,
+                const int* active);
+
 void coil_rhs(ect_ctx* c, const ect_coil& coil, const double* h_z, int k, double2* d_rhs);
 void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b, const double* cur,
              int n_pos, double* h_dz, double* h_dz_emf);

@@ -131,7 +131,69 @@ __global__ void k_fill_bsr(const unsigned long long* __restrict__ keys, const in
     }
 }
 
+
+// per-tet coefficients of the defect configuration (NaN = background)
+void defect_coefficients(const std::vector<double>& s0, const std::vector<double>& n0, const double* sigma_d,
+                         const double* nu_d, std::vector<double>& s1, std::vector<double>& n1) {
+    s1 = s0;
+    n1 = n0;
+    for (size_t t = 0; t < s0.size(); ++t) {
+        if (sigma_d && !std::isnan(sigma_d[t])) {
+            ECT_REQUIRE(std::isfinite(sigma_d[t]) && sigma_d[t] >= 0.0, ECT_ERR_ARG, "bad defect sigma");
+            s1[t] = sigma_d[t];
+        }
+        if (nu_d && !std::isnan(nu_d[t])) {
+            ECT_REQUIRE(std::isfinite(nu_d[t]) && nu_d[t] > 0.0, ECT_ERR_ARG, "bad defect nu");
+            n1[t] = nu_d[t];
+        }
+    }
+}
+
+// coefficients, conducting nodes and constraint mask of configuration m
+void upload_config(ect_ctx* c, int m, const std::vector<double>& s, const std::vector<double>& n) {
+    const int64_t N = c->n_nodes, T = c->n_tets;
+    Matrix& M = c->mat[m];
+    M.h_cond.assign(N, 0);
+    for (int64_t t = 0; t < T; ++t)
+        if (s[t] > 0.0)
+            for (int a = 0; a < 4; ++a) M.h_cond[c->h_tets[4 * t + a]] = 1;
+    std::vector<uint8_t> fm(N);
+    for (int64_t i = 0; i < N; ++i) fm[i] = (uint8_t)((c->h_bc[i] & 7) | (M.h_cond[i] ? 0 : 8));
+    cudaStream_t st = c->stream;
+    M.sigma.alloc(sizeof(double) * T);
+    M.nu.alloc(sizeof(double) * T);
+    M.fixmask.alloc(N);
+    ECT_CUDA(cudaMemcpyAsync(M.sigma.p, s.data(), M.sigma.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(M.nu.p, n.data(), M.nu.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(M.fixmask.p, fm.data(), N, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaStreamSynchronize(st));
+    M.assembled = M.pc_f64 = M.pc_f32 = false;
+}
+
+// Omega_d: the tets whose coefficients differ between the two configurations
+void upload_defect_list(ect_ctx* c, const std::vector<double>& s1, const std::vector<double>& n1) {
+    std::vector<int32_t> od;
+    for (int64_t t = 0; t < c->n_tets; ++t)
+        if (s1[t] != c->h_sigma0[t] || n1[t] != c->h_nu0[t]) od.push_back((int32_t)t);
+    c->n_omega_d = (int64_t)od.size();
+    c->omega_d.alloc(sizeof(int32_t) * std::max<size_t>(od.size(), 1));
+    if (!od.empty())
+        ECT_CUDA(cudaMemcpyAsync(c->omega_d.p, od.data(), sizeof(int32_t) * od.size(), cudaMemcpyHostToDevice,
+                                 c->stream));
+    ECT_CUDA(cudaStreamSynchronize(c->stream));
+}
+
 }  // namespace
+
+void set_defect(ect_ctx* c, const double* sigma_d, const double* nu_d) {
+    ECT_REQUIRE(c->mesh_set, ECT_ERR_STATE, "ect_set_mesh must come first");
+    std::vector<double> s1, n1;
+    defect_coefficients(c->h_sigma0, c->h_nu0, sigma_d, nu_d, s1, n1);
+    workspace_free(c);
+    c->mat[1].reset();
+    upload_config(c, 1, s1, n1);
+    upload_defect_list(c, s1, n1);
+}
 
 void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                 const double* sigma, const double* nu, const double* sigma_d, const double* nu_d,
@@ -163,31 +225,10 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     }
     ECT_REQUIRE(maxb <= 16, ECT_ERR_ARG, "a subdomain block has more than 16 nodes");
 
-    // effective coefficients of the two configurations, conducting nodes, Omega_d
-    std::vector<double> s0(sigma, sigma + n_tets), n0(nu, nu + n_tets), s1(s0), n1(n0);
-    std::vector<int32_t> od;
-    for (int64_t t = 0; t < n_tets; ++t) {
-        if (sigma_d && !std::isnan(sigma_d[t])) {
-            ECT_REQUIRE(std::isfinite(sigma_d[t]) && sigma_d[t] >= 0.0, ECT_ERR_ARG, "bad defect sigma");
-            s1[t] = sigma_d[t];
-        }
-        if (nu_d && !std::isnan(nu_d[t])) {
-            ECT_REQUIRE(std::isfinite(nu_d[t]) && nu_d[t] > 0.0, ECT_ERR_ARG, "bad defect nu");
-            n1[t] = nu_d[t];
-        }
-        if (s1[t] != s0[t] || n1[t] != n0[t]) od.push_back((int32_t)t);
-    }
-    std::vector<uint8_t> fm[2], condv[2];
-    for (int m = 0; m < 2; ++m) {
-        const std::vector<double>& s = m ? s1 : s0;
-        std::vector<uint8_t>& cond = condv[m];
-        cond.assign(n_nodes, 0);
-        for (int64_t t = 0; t < n_tets; ++t)
-            if (s[t] > 0.0)
-                for (int a = 0; a < 4; ++a) cond[tets[4 * t + a]] = 1;
-        fm[m].resize(n_nodes);
-        for (int64_t n = 0; n < n_nodes; ++n) fm[m][n] = (uint8_t)((bc_mask[n] & 7) | (cond[n] ? 0 : 8));
-    }
+    // effective coefficients of the two configurations
+    std::vector<double> s0(sigma, sigma + n_tets), n0(nu, nu + n_tets);
+    std::vector<double> s1, n1;
+    defect_coefficients(s0, n0, sigma_d, nu_d, s1, n1);
 
     // reset state
     c->mesh_set = false;
@@ -211,20 +252,13 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     ECT_CUDA(cudaMemcpyAsync(c->bc.p, bc_mask, n_nodes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->block_ptr.p, bptr.data(), c->block_ptr.bytes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->pinv_off.p, poff.data(), c->pinv_off.bytes, cudaMemcpyHostToDevice, st));
-    for (int m = 0; m < 2; ++m) {
-        Matrix& M = c->mat[m];
-        M.h_cond = condv[m];
-        M.sigma.alloc(sizeof(double) * n_tets);
-        M.nu.alloc(sizeof(double) * n_tets);
-        M.fixmask.alloc(n_nodes);
-        ECT_CUDA(cudaMemcpyAsync(M.sigma.p, (m ? s1 : s0).data(), M.sigma.bytes, cudaMemcpyHostToDevice, st));
-        ECT_CUDA(cudaMemcpyAsync(M.nu.p, (m ? n1 : n0).data(), M.nu.bytes, cudaMemcpyHostToDevice, st));
-        ECT_CUDA(cudaMemcpyAsync(M.fixmask.p, fm[m].data(), n_nodes, cudaMemcpyHostToDevice, st));
-    }
-    c->n_omega_d = (int64_t)od.size();
-    c->omega_d.alloc(sizeof(int32_t) * std::max<size_t>(od.size(), 1));
-    if (!od.empty())
-        ECT_CUDA(cudaMemcpyAsync(c->omega_d.p, od.data(), sizeof(int32_t) * od.size(), cudaMemcpyHostToDevice, st));
+    c->h_tets.assign(tets, tets + 4 * n_tets);
+    c->h_bc.assign(bc_mask, bc_mask + n_nodes);
+    c->h_sigma0 = s0;
+    c->h_nu0 = n0;
+    upload_config(c, 0, s0, n0);
+    upload_config(c, 1, s1, n1);
+    upload_defect_list(c, s1, n1);
 
     // geometry
     c->geo.alloc(sizeof(double) * 16 * n_tets);

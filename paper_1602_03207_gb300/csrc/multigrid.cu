@@ -1,0 +1,503 @@
+// Aggregation multigrid preconditioner built on the subdomain blocks.
+//
+// The paper partitions the mesh into subdomains (Sec. 3, Step 2).  Here the
+// subdomains are (i) the smoothing blocks of the finest level (block-Jacobi
+// with dense block inverses, kernel (c)) and (ii) the aggregates of the first
+// coarsening: every subdomain becomes one coarse node with four unknowns
+// (A_x, A_y, A_z, V).  The tentative prolongator carries the near-null
+// vectors of the operator (a constant field per component): on the finest
+// level its weights are 1/t (t the diagonal scaling) on free unknowns and 0
+// on constrained ones, on coarser levels 1 on non-empty and 0 on empty coarse
+// unknowns.  The coarse operator is the Galerkin product E = P^T A P (plus
+// the identity on empty coarse unknowns); it is again a matrix of 4x4 complex
+// blocks, so the same BSR SpMV and block kernels serve every level.  Coarse
+// levels are aggregated greedily (a seed takes its not yet aggregated
+// neighbours in increasing order, at most 8 nodes) and renumbered so that
+// aggregates are contiguous; the coarsest level (<= 2048 unknowns) is
+// inverted densely.  The cycle is a W-cycle with one block-Jacobi sweep
+// before and after the coarse corrections.
+//
+// Setup runs once per matrix: patterns and aggregation on the host (integer
+// work), Galerkin values on the device (one thread per coarse block sums its
+// fine blocks in a fixed order).
+#include <algorithm>
+#include <numeric>
+#include <deque>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int AGG_SIZE = 8;
+constexpr int64_t MAX_COARSE_DOFS = 2048;
+
+// coarse block values: sum over the fine blocks mapped to each coarse block of
+// w_i[p] A_ij[p][q] w_j[q]; identity on empty coarse unknowns of diagonal blocks
+__global__ void k_galerkin(const int32_t* __restrict__ cptr, const int32_t* __restrict__ clist,
+                           const int32_t* __restrict__ frow, const int32_t* __restrict__ fcol,
+                           const double2* __restrict__ fval, const double* __restrict__ w, int64_t nnzc,
+                           const int32_t* __restrict__ crow_of_slot, const int32_t* __restrict__ ccol,
+                           const uint8_t* __restrict__ cempty, double2* __restrict__ cval) {
+    const int64_t cs = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cs >= nnzc) return;
+    double re[16], im[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) re[e] = im[e] = 0.0;
+    for (int32_t q = cptr[cs]; q < cptr[cs + 1]; ++q) {
+        const int32_t s = clist[q];
+        const int64_t i = frow[s], j = fcol[s];
+        double wi[4], wj[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            wi[p] = w[4 * i + p];
+            wj[p] = w[4 * j + p];
+        }
+        const double2* v = fval + 16 * (int64_t)s;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const double f = wi[p] * wj[r];
+                re[4 * p + r] += f * v[4 * p + r].x;
+                im[4 * p + r] += f * v[4 * p + r].y;
+            }
+    }
+    const int32_t I = crow_of_slot[cs], J = ccol[cs];
+    double2* out = cval + 16 * cs;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            double2 v = make_double2(re[4 * p + r], im[4 * p + r]);
+            if (I == J && p == r && cempty[4 * (int64_t)I + p]) v = make_double2(1.0, 0.0);
+            out[4 * p + r] = v;
+        }
+}
+
+// rc[r][4 I + p] = sum over the fine nodes i of coarse node I of w[4 i + p] t[r][4 i + p]
+template <typename T>
+__global__ void k_restrict(const C<T>* __restrict__ t, int64_t ldf, const int32_t* __restrict__ lo,
+                           const int32_t* __restrict__ hi, const T* __restrict__ w, int64_t nc_nodes, int k,
+                           const int* __restrict__ active, C<T>* __restrict__ rc, int64_t ldc) {
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (d >= 4 * nc_nodes || (active && !active[r])) return;
+    const int64_t I = d >> 2;
+    const int p = (int)(d & 3);
+    C<T> s = czero<T>();
+    for (int32_t i = lo[I]; i < hi[I]; ++i) {
+        const T wi = w[4 * (int64_t)i + p];
+        const C<T> v = t[(int64_t)r * ldf + 4 * (int64_t)i + p];
+        s.x += wi * v.x;
+        s.y += wi * v.y;
+    }
+    rc[(int64_t)r * ldc + d] = s;
+}
+
+// z[r][4 i + p] += w[4 i + p] zc[r][4 agg(i) + p]
+template <typename T>
+__global__ void k_prolong(C<T>* __restrict__ z, int64_t ldf, const int32_t* __restrict__ node_agg,
+                          const T* __restrict__ w, int64_t n_nodes, const C<T>* __restrict__ zc, int64_t ldc,
+                          const int* __restrict__ active) {
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (d >= 4 * n_nodes || (active && !active[r])) return;
+    const T wi = w[d];
+    if (wi == T(0)) return;
+    const C<T> v = zc[(int64_t)r * ldc + 4 * (int64_t)node_agg[d >> 2] + (d & 3)];
+    C<T>& o = z[(int64_t)r * ldf + d];
+    o.x += wi * v.x;
+    o.y += wi * v.y;
+}
+
+__global__ void k_finest_weights(const double* __restrict__ t, const uint8_t* __restrict__ fixmask, int64_t N,
+                                 double* __restrict__ w) {
+    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= 4 * N) return;
+    const int p = (int)(d & 3);
+    const bool fixed = (fixmask[d >> 2] >> p) & 1u;
+    w[d] = fixed ? 0.0 : 1.0 / t[d];
+}
+
+__global__ void k_d2f_real(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) b[e] = (float)a[e];
+}
+
+// scatter BSR blocks into a dense row-major nc x nc matrix
+__global__ void k_densify(const int32_t* __restrict__ crow_of_slot, const int32_t* __restrict__ ccol,
+                          const double2* __restrict__ cval, int64_t nnzc, int64_t nc, double2* __restrict__ dense) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= 16 * nnzc) return;
+    const int64_t s = e >> 4;
+    const int p = (int)((e >> 2) & 3), q = (int)(e & 3);
+    dense[(4 * (int64_t)crow_of_slot[s] + p) * nc + 4 * (int64_t)ccol[s] + q] = cval[e];
+}
+
+}  // namespace
+
+struct MgLevel {
+    int64_t n = 0, nnzb = 0, n_agg = 0, n_next = 0;
+    int max_agg = 0;
+    const int32_t* rp = nullptr;
+    const int32_t* col = nullptr;
+    const double2* val64 = nullptr;
+    const float2* val32 = nullptr;
+    DevBuf rp_own, col_own, val_own, val32_own;
+    std::vector<int32_t> h_rp, h_col, h_agg_ptr;
+    std::vector<uint8_t> h_free;             // 4n: unknown carries a near-null weight
+    const int32_t* d_agg_ptr = nullptr;
+    const int64_t* d_pinv_off = nullptr;
+    const double2* d_pinv64 = nullptr;
+    const float2* d_pinv32 = nullptr;
+    DevBuf agg_ptr_own, pinv_off_own, pinv64_own, pinv32_own;
+    DevBuf node_agg, clo, chi, w64, w32;
+    DevBuf r, z, t;                          // cycle vectors (k right-hand sides)
+};
+
+struct Multigrid {
+    std::deque<MgLevel> L;                   // all levels but the coarsest (stable references)
+    int64_t nc = 0;                          // unknowns of the coarsest level
+    DevBuf einv64, einv32, rc, zc;
+    int64_t kcap = 0;
+    bool f32 = false;
+};
+
+void mg_free(Matrix& M) {
+    delete M.mg;
+    M.mg = nullptr;
+}
+
+namespace {
+
+template <typename T>
+const C<T>* lvl_pinv(const MgLevel& L);
+template <>
+const double2* lvl_pinv<double>(const MgLevel& L) { return L.d_pinv64; }
+template <>
+const float2* lvl_pinv<float>(const MgLevel& L) { return L.d_pinv32; }
+template <typename T>
+const C<T>* lvl_val(const MgLevel& L);
+template <>
+const double2* lvl_val<double>(const MgLevel& L) { return L.val64; }
+template <>
+const float2* lvl_val<float>(const MgLevel& L) { return L.val32; }
+template <typename T>
+const T* lvl_w(const MgLevel& L);
+template <>
+const double* lvl_w<double>(const MgLevel& L) { return L.w64.as<double>(); }
+template <>
+const float* lvl_w<float>(const MgLevel& L) { return L.w32.as<float>(); }
+
+void level_smoother(cudaStream_t st, MgLevel& L, bool f32) {
+    // block inverses of the level's matrix over its (contiguous) aggregates
+    const int64_t na = (int64_t)L.h_agg_ptr.size() - 1;
+    L.n_agg = na;
+    std::vector<int64_t> poff(na + 1, 0);
+    int mx = 0;
+    for (int64_t a = 0; a < na; ++a) {
+        const int sz = L.h_agg_ptr[a + 1] - L.h_agg_ptr[a];
+        mx = std::max(mx, sz);
+        poff[a + 1] = poff[a] + (int64_t)(4 * sz) * (4 * sz);
+    }
+    L.max_agg = mx;
+    L.agg_ptr_own.alloc(sizeof(int32_t) * (na + 1));
+    L.pinv_off_own.alloc(sizeof(int64_t) * (na + 1));
+    ECT_CUDA(cudaMemcpyAsync(L.agg_ptr_own.p, L.h_agg_ptr.data(), L.agg_ptr_own.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(L.pinv_off_own.p, poff.data(), L.pinv_off_own.bytes, cudaMemcpyHostToDevice, st));
+    L.pinv64_own.alloc(sizeof(double2) * poff.back());
+    if (f32) L.pinv32_own.alloc(sizeof(float2) * poff.back());
+    block_inverses(st, L.rp, L.col, L.val64, L.agg_ptr_own.as<int32_t>(), L.pinv_off_own.as<int64_t>(), na, mx,
+                   L.pinv64_own.as<double2>(), f32 ? L.pinv32_own.as<float2>() : nullptr);
+    L.d_agg_ptr = L.agg_ptr_own.as<int32_t>();
+    L.d_pinv_off = L.pinv_off_own.as<int64_t>();
+    L.d_pinv64 = L.pinv64_own.as<double2>();
+    L.d_pinv32 = f32 ? L.pinv32_own.as<float2>() : nullptr;
+}
+
+template <typename T>
+void to_device(DevBuf& b, const std::vector<T>& h, cudaStream_t st) {
+    b.alloc(sizeof(T) * std::max<size_t>(h.size(), 1));
+    if (!h.empty()) ECT_CUDA(cudaMemcpyAsync(b.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+}
+
+}  // namespace
+
+void mg_setup(ect_ctx* c, int which, bool f32) {
+    Matrix& M = c->mat[which];
+    mg_free(M);
+    cudaStream_t st = c->stream;
+    Multigrid* G = new Multigrid();
+    M.mg = G;
+    G->f32 = f32;
+    // ---- finest level: the matrix, its subdomain blocks and their inverses
+    G->L.emplace_back();
+    {
+        MgLevel& L = G->L.back();
+        L.n = c->n_nodes;
+        L.nnzb = c->nnzb;
+        L.rp = c->row_ptr.as<int32_t>();
+        L.col = c->col.as<int32_t>();
+        L.val64 = M.sval.as<double2>();
+        L.val32 = f32 ? M.sval32.as<float2>() : nullptr;
+        L.h_rp = c->h_row_ptr;
+        L.h_col = c->h_col;
+        L.h_agg_ptr = c->h_block_ptr;
+        L.n_agg = c->n_blocks;
+        L.max_agg = c->max_block_nodes;
+        L.d_agg_ptr = c->block_ptr.as<int32_t>();
+        L.d_pinv_off = c->pinv_off.as<int64_t>();
+        L.d_pinv64 = M.pinv.as<double2>();
+        L.d_pinv32 = f32 ? M.pinv32.as<float2>() : nullptr;
+        L.h_free.resize(4 * L.n);
+        for (int64_t i = 0; i < L.n; ++i)
+            for (int p = 0; p < 4; ++p)
+                L.h_free[4 * i + p] = p < 3 ? !((c->h_bc[i] >> p) & 1) : (M.h_cond[i] != 0);
+        L.w64.alloc(sizeof(double) * 4 * L.n);
+        k_finest_weights<<<grid_for(4 * L.n, 256), 256, 0, st>>>(M.t.as<double>(), M.fixmask.as<uint8_t>(), L.n,
+                                                                 L.w64.as<double>());
+        ECT_CHECK_LAUNCH();
+        if (f32) {
+            L.w32.alloc(sizeof(float) * 4 * L.n);
+            k_d2f_real<<<grid_for(4 * L.n, 256), 256, 0, st>>>(L.w64.as<double>(), L.w32.as<float>(), 4 * L.n);
+        }
+    }
+    // ---- coarsen until the coarse level has at most MAX_COARSE_DOFS unknowns
+    for (int depth = 0; depth < 32; ++depth) {
+        MgLevel& L = G->L.back();
+        const int64_t n = L.n, na = (int64_t)L.h_agg_ptr.size() - 1;
+        std::vector<int32_t> agg(n);
+        for (int64_t a = 0; a < na; ++a)
+            for (int32_t i = L.h_agg_ptr[a]; i < L.h_agg_ptr[a + 1]; ++i) agg[i] = (int32_t)a;
+        // provisional coarse pattern (coarse node = aggregate index) and empty unknowns
+        std::vector<std::vector<int32_t>> crow(na);
+        std::vector<uint8_t> empty(4 * na, 1);
+        for (int64_t a = 0; a < na; ++a) {
+            std::vector<int32_t>& cr = crow[a];
+            for (int32_t i = L.h_agg_ptr[a]; i < L.h_agg_ptr[a + 1]; ++i) {
+                for (int p = 0; p < 4; ++p)
+                    if (L.h_free[4 * i + p]) empty[4 * a + p] = 0;
+                for (int32_t s = L.h_rp[i]; s < L.h_rp[i + 1]; ++s) cr.push_back(agg[L.h_col[s]]);
+            }
+            std::sort(cr.begin(), cr.end());
+            cr.erase(std::unique(cr.begin(), cr.end()), cr.end());
+        }
+        const bool coarsest = 4 * na <= MAX_COARSE_DOFS;
+        // aggregation of the coarse graph and renumbering (aggregates contiguous)
+        std::vector<int32_t> cagg(na, -1), order(na), newid(na);
+        if (coarsest) {
+            std::iota(order.begin(), order.end(), 0);
+        } else {
+            int32_t nca = 0;
+            for (int64_t I = 0; I < na; ++I) {
+                if (cagg[I] >= 0) continue;
+                int members = 1;
+                cagg[I] = nca;
+                for (int32_t J : crow[I]) {
+                    if (members >= AGG_SIZE) break;
+                    if (J != I && cagg[J] < 0) {
+                        cagg[J] = nca;
+                        ++members;
+                    }
+                }
+                ++nca;
+            }
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cagg[a] < cagg[b]; });
+        }
+        for (int64_t k = 0; k < na; ++k) newid[order[k]] = (int32_t)k;
+        // final coarse pattern in the new numbering
+        std::vector<int32_t> nrp(na + 1, 0), ncol, ncrow;
+        for (int64_t k = 0; k < na; ++k) {
+            std::vector<int32_t> cols;
+            for (int32_t J : crow[order[k]]) cols.push_back(newid[J]);
+            std::sort(cols.begin(), cols.end());
+            for (int32_t J : cols) {
+                ncol.push_back(J);
+                ncrow.push_back((int32_t)k);
+            }
+            nrp[k + 1] = (int32_t)ncol.size();
+        }
+        const int64_t nnzc = (int64_t)ncol.size();
+        std::vector<uint8_t> nempty(4 * na);
+        for (int64_t k = 0; k < na; ++k)
+            for (int p = 0; p < 4; ++p) nempty[4 * k + p] = empty[4 * order[k] + p];
+        // fine block -> coarse block map, then the per-coarse-block lists (fine blocks ascending)
+        std::vector<int32_t> cslot(L.nnzb), frow(L.nnzb);
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t I = newid[agg[i]];
+            const int32_t* b0 = ncol.data() + nrp[I];
+            const int32_t* b1 = ncol.data() + nrp[I + 1];
+            for (int32_t s = L.h_rp[i]; s < L.h_rp[i + 1]; ++s) {
+                const int32_t J = newid[agg[L.h_col[s]]];
+                cslot[s] = nrp[I] + (int32_t)(std::lower_bound(b0, b1, J) - b0);
+                frow[s] = (int32_t)i;
+            }
+        }
+        std::vector<int32_t> cptr(nnzc + 1, 0), clist(L.nnzb);
+        for (int64_t s = 0; s < L.nnzb; ++s) ++cptr[cslot[s] + 1];
+        for (int64_t q = 0; q < nnzc; ++q) cptr[q + 1] += cptr[q];
+        {
+            std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+            for (int64_t s = 0; s < L.nnzb; ++s) clist[fill[cslot[s]]++] = (int32_t)s;
+        }
+        DevBuf d_cptr, d_clist, d_frow, d_crow, d_ccol, d_cempty, cval;
+        to_device(d_cptr, cptr, st);
+        to_device(d_clist, clist, st);
+        to_device(d_frow, frow, st);
+        to_device(d_crow, ncrow, st);
+        to_device(d_ccol, ncol, st);
+        to_device(d_cempty, nempty, st);
+        cval.alloc(sizeof(double2) * 16 * std::max<int64_t>(nnzc, 1));
+        k_galerkin<<<grid_for(nnzc, 128), 128, 0, st>>>(d_cptr.as<int32_t>(), d_clist.as<int32_t>(),
+                                                         d_frow.as<int32_t>(), L.col, L.val64, L.w64.as<double>(),
+                                                         nnzc, d_crow.as<int32_t>(), d_ccol.as<int32_t>(),
+                                                         d_cempty.as<uint8_t>(), cval.as<double2>());
+        ECT_CHECK_LAUNCH();
+        // restriction / prolongation maps of this level
+        std::vector<int32_t> nagg(n), lo(na), hi(na);
+        for (int64_t i = 0; i < n; ++i) nagg[i] = newid[agg[i]];
+        for (int64_t k = 0; k < na; ++k) {
+            lo[k] = L.h_agg_ptr[order[k]];
+            hi[k] = L.h_agg_ptr[order[k] + 1];
+        }
+        to_device(L.node_agg, nagg, st);
+        to_device(L.clo, lo, st);
+        to_device(L.chi, hi, st);
+        L.n_next = na;
+        ECT_CUDA(cudaStreamSynchronize(st));
+        if (coarsest) {
+            const int64_t nc = 4 * na;
+            G->nc = nc;
+            G->einv64.alloc(sizeof(double2) * nc * nc);
+            ECT_CUDA(cudaMemsetAsync(G->einv64.p, 0, G->einv64.bytes, st));
+            k_densify<<<grid_for(16 * nnzc, 256), 256, 0, st>>>(d_crow.as<int32_t>(), d_ccol.as<int32_t>(),
+                                                                cval.as<double2>(), nnzc, nc, G->einv64.as<double2>());
+            ECT_CHECK_LAUNCH();
+            dense_inverse(st, G->einv64.as<double2>(), nc);
+            if (f32) {
+                G->einv32.alloc(sizeof(float2) * nc * nc);
+                to_f32(st, G->einv64.as<double2>(), G->einv32.as<float2>(), nc * nc);
+            }
+            ECT_CUDA(cudaStreamSynchronize(st));
+            return;
+        }
+        // next level
+        std::vector<int32_t> nagg_ptr(1, 0);
+        for (int64_t k = 1; k <= na; ++k)
+            if (k == na || cagg[order[k]] != cagg[order[k - 1]]) nagg_ptr.push_back((int32_t)k);
+        G->L.emplace_back();
+        MgLevel& Lc = G->L.back();
+        Lc.n = na;
+        Lc.nnzb = nnzc;
+        Lc.h_rp = nrp;
+        Lc.h_col = ncol;
+        Lc.h_agg_ptr = nagg_ptr;
+        to_device(Lc.rp_own, nrp, st);
+        to_device(Lc.col_own, ncol, st);
+        Lc.rp = Lc.rp_own.as<int32_t>();
+        Lc.col = Lc.col_own.as<int32_t>();
+        Lc.val_own.alloc(cval.bytes);
+        ECT_CUDA(cudaMemcpyAsync(Lc.val_own.p, cval.p, cval.bytes, cudaMemcpyDeviceToDevice, st));
+        Lc.val64 = Lc.val_own.as<double2>();
+        if (f32) {
+            Lc.val32_own.alloc(sizeof(float2) * 16 * nnzc);
+            to_f32(st, Lc.val64, Lc.val32_own.as<float2>(), 16 * nnzc);
+            Lc.val32 = Lc.val32_own.as<float2>();
+        }
+        Lc.h_free.resize(4 * na);
+        std::vector<double> w(4 * na);
+        std::vector<float> wf(4 * na);
+        for (int64_t d = 0; d < 4 * na; ++d) {
+            Lc.h_free[d] = !nempty[d];
+            w[d] = nempty[d] ? 0.0 : 1.0;
+            wf[d] = (float)w[d];
+        }
+        to_device(Lc.w64, w, st);
+        to_device(Lc.w32, wf, st);
+        level_smoother(st, Lc, f32);
+        ECT_CUDA(cudaStreamSynchronize(st));
+    }
+    throw EctError{ECT_ERR_ARG, "multigrid did not reach the coarsest size"};
+}
+
+void mg_scratch(Matrix& M, int k) {
+    Multigrid* G = M.mg;
+    if (!G || G->kcap >= k) return;
+    for (size_t l = 0; l < G->L.size(); ++l) {
+        MgLevel& L = G->L[l];
+        const size_t bytes = sizeof(double2) * 4 * (size_t)L.n * k;
+        L.t.alloc(bytes);
+        if (l > 0) {
+            L.r.alloc(bytes);
+            L.z.alloc(bytes);
+        }
+    }
+    G->rc.alloc(sizeof(double2) * G->nc * k);
+    G->zc.alloc(sizeof(double2) * G->nc * k);
+    G->kcap = k;
+}
+
+namespace {
+
+template <typename T>
+void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int k, int tile, const int* active) {
+    if (l == G->L.size()) {
+        const C<T>* e = std::is_same<T, double>::value ? (const C<T>*)G->einv64.p : (const C<T>*)G->einv32.p;
+        dense_gemv<T>(st, e, G->nc, r, z, k, tile, active);
+        return;
+    }
+    MgLevel& L = G->L[l];
+    const int64_t ld = 4 * L.n;
+    const bool last = (l + 1 == G->L.size());
+    const int64_t ldn = last ? G->nc : 4 * G->L[l + 1].n;
+    C<T>* rn = last ? (C<T>*)G->rc.p : (C<T>*)G->L[l + 1].r.p;
+    C<T>* zn = last ? (C<T>*)G->zc.p : (C<T>*)G->L[l + 1].z.p;
+    C<T>* t = (C<T>*)L.t.p;
+    const C<T>* val = lvl_val<T>(L);
+    const T* w = lvl_w<T>(L);
+    block_apply<T>(st, L.d_agg_ptr, L.d_pinv_off, lvl_pinv<T>(L), L.n_agg, r, z, k, ld, tile, active, false);
+    const int gamma = last ? 1 : 2;
+    for (int g = 0; g < gamma; ++g) {
+        if (std::is_same<T, double>::value)
+            bsr_spmv_f64(st, L.rp, L.col, (const double2*)val, L.n, (const double2*)z, (const double2*)r, (double2*)t,
+                         k, ld, tile, active);
+        else
+            bsr_spmv_f32(st, L.rp, L.col, (const float2*)val, L.n, (const float2*)z, (const float2*)r, (float2*)t, k,
+                         ld, tile, active);
+        k_restrict<T><<<dim3(grid_for(4 * L.n_next, 256), k), 256, 0, st>>>(
+            t, ld, L.clo.as<int32_t>(), L.chi.as<int32_t>(), w, L.n_next, k, active, rn, ldn);
+        cycle<T>(st, G, l + 1, rn, zn, k, tile, active);
+        k_prolong<T><<<dim3(grid_for(4 * L.n, 256), k), 256, 0, st>>>(z, ld, L.node_agg.as<int32_t>(), w, L.n, zn, ldn,
+                                                                        active);
+    }
+    if (std::is_same<T, double>::value)
+        bsr_spmv_f64(st, L.rp, L.col, (const double2*)val, L.n, (const double2*)z, (const double2*)r, (double2*)t, k,
+                     ld, tile, active);
+    else
+        bsr_spmv_f32(st, L.rp, L.col, (const float2*)val, L.n, (const float2*)z, (const float2*)r, (float2*)t, k, ld,
+                     tile, active);
+    block_apply<T>(st, L.d_agg_ptr, L.d_pinv_off, lvl_pinv<T>(L), L.n_agg, t, z, k, ld, tile, active, true);
+    ECT_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void mg_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld, int tile, const int* active) {
+    Matrix& M = c->mat[which];
+    ECT_REQUIRE(M.mg && M.mg->kcap >= k, ECT_ERR_STATE, "multigrid scratch not ready (internal)");
+    ECT_REQUIRE(ld == 4 * c->n_nodes, ECT_ERR_ARG, "multigrid vectors must be packed");
+    cycle<double>(c->stream, M.mg, 0, r, z, k, tile, active);
+}
+
+void mg_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld, int tile, const int* active) {
+    Matrix& M = c->mat[which];
+    ECT_REQUIRE(M.mg && M.mg->kcap >= k && M.mg->f32, ECT_ERR_STATE, "FP32 multigrid not ready");
+    ECT_REQUIRE(ld == 4 * c->n_nodes, ECT_ERR_ARG, "multigrid vectors must be packed");
+    cycle<float>(c->stream, M.mg, 0, r, z, k, tile, active);
+}
+
+int mg_levels(const Matrix& M) { return M.mg ? (int)M.mg->L.size() + 1 : 0; }
+
+bool mg_ready(const Matrix& M, int k) { return M.mg && M.mg->kcap >= k; }

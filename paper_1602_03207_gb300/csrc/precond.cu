@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
                                                     C<T>* __restrict__ z, int k, int64_t ld,
                                                     const int* __restrict__ active,
                                                     const int32_t* __restrict__ blk_c, const C<T>* __restrict__ zc,
-                                                    int64_t nc, const T* __restrict__ zv) {
+                                                    int64_t nc, const T* __restrict__ zv, int accumulate) {
     __shared__ C<T> rs[KT][64];
     const int blk = blockIdx.x, tid = threadIdx.x;
     const int r0 = blockIdx.y * KT;
@@ -160,7 +160,10 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
     }
 #pragma unroll
     for (int q = 0; q < KT; ++q)
-        if (on[q]) z[(int64_t)(r0 + q) * ld + base + tid] = acc[q];
+        if (on[q]) {
+            C<T>* zp = z + (int64_t)(r0 + q) * ld + base + tid;
+            *zp = accumulate ? cadd(*zp, acc[q]) : acc[q];
+        }
 }
 
 // coarse restriction: rc[r][c] = sum over the group's nodes of zv[i] * r[r][4i+3]
@@ -320,10 +323,10 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
     }
     const int32_t* bc = M.blk_c.as<int32_t>();
     switch (kt) {
-        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
-        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
-        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
-        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv); break;
+        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
+        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
+        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
+        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
     }
     ECT_CHECK_LAUNCH();
 }
@@ -416,6 +419,82 @@ void coarse_setup(ect_ctx* c, int which, int group) {
 
 }  // namespace
 
+void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, const double2* sval, const int32_t* bptr,
+                    const int64_t* poff, int64_t n_blocks, int max_block_nodes, double2* pinv, float2* pinv32) {
+    const int bmax = 4 * max_block_nodes;
+    ECT_REQUIRE(bmax <= 64, ECT_ERR_ARG, "smoothing block larger than 16 nodes");
+    const size_t smem = sizeof(double2) * (size_t)bmax * 2 * bmax;
+    ECT_CUDA(cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DevBuf flag;
+    flag.alloc(sizeof(int));
+    ECT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    k_block_inverse<<<(unsigned)n_blocks, 256, smem, st>>>(rp, col, sval, bptr, poff, pinv, pinv32, flag.as<int>());
+    ECT_CHECK_LAUNCH();
+    int h = 0;
+    ECT_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ECT_CUDA(cudaStreamSynchronize(st));
+    ECT_REQUIRE(!h, ECT_ERR_BREAKDOWN, "a smoothing block is singular");
+}
+
+template <typename T>
+void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, const C<T>* pinv, int64_t n_blocks,
+                 const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate) {
+    const int kt = pick_ptile(k, rhs_tile);
+    dim3 grid((unsigned)n_blocks, (unsigned)((k + kt - 1) / kt));
+    const int acc = accumulate ? 1 : 0;
+    switch (kt) {
+        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
+        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
+        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
+        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
+    }
+    ECT_CHECK_LAUNCH();
+}
+template void block_apply<double>(cudaStream_t, const int32_t*, const int64_t*, const double2*, int64_t, const double2*,
+                                  double2*, int, int64_t, int, const int*, bool);
+template void block_apply<float>(cudaStream_t, const int32_t*, const int64_t*, const float2*, int64_t, const float2*,
+                                 float2*, int, int64_t, int, const int*, bool);
+
+// in-place dense inverse of a (n x n, complex128, row-major) on the device
+void dense_inverse(cudaStream_t st, double2* a, int64_t n) {
+    DevBuf rowk, colk, flag;
+    rowk.alloc(sizeof(double2) * n);
+    colk.alloc(sizeof(double2) * n);
+    flag.alloc(sizeof(int));
+    ECT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    for (int64_t kk = 0; kk < n; ++kk) {
+        k_gj_save<<<grid_for(n, 256), 256, 0, st>>>(a, n, kk, rowk.as<double2>(), colk.as<double2>(), flag.as<int>());
+        k_gj_update<<<grid_for(n * n, 256), 256, 0, st>>>(a, n, kk, rowk.as<double2>(), colk.as<double2>());
+    }
+    ECT_CHECK_LAUNCH();
+    int bad = 0;
+    ECT_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ECT_CUDA(cudaStreamSynchronize(st));
+    ECT_REQUIRE(!bad, ECT_ERR_BREAKDOWN, "the coarsest matrix has a zero pivot");
+}
+
+void to_f32(cudaStream_t st, const double2* a, float2* b, int64_t n) {
+    k_d2f_vec<<<grid_for(n, 256), 256, 0, st>>>(a, b, n);
+    ECT_CHECK_LAUNCH();
+}
+
+// z[r] = Einv r[r] (dense, symmetric Einv) for k vectors of length nc
+template <typename T>
+void dense_gemv(cudaStream_t st, const C<T>* einv, int64_t nc, const C<T>* r, C<T>* z, int k, int rhs_tile,
+                const int* active) {
+    const int kt = pick_ptile(k, rhs_tile);
+    dim3 g2(grid_for(nc, 256), (unsigned)((k + kt - 1) / kt));
+    switch (kt) {
+        case 8: k_coarse_gemv<T, 8><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
+        case 4: k_coarse_gemv<T, 4><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
+        case 2: k_coarse_gemv<T, 2><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
+        default: k_coarse_gemv<T, 1><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
+    }
+    ECT_CHECK_LAUNCH();
+}
+template void dense_gemv<double>(cudaStream_t, const double2*, int64_t, const double2*, double2*, int, int, const int*);
+template void dense_gemv<float>(cudaStream_t, const float2*, int64_t, const float2*, float2*, int, int, const int*);
+
 void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) {
     ECT_REQUIRE(which == ECT_VACUUM || which == ECT_DEFECT, ECT_ERR_ARG, "bad which");
     Matrix& M = c->mat[which];
@@ -439,23 +518,13 @@ void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) 
     ECT_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     ECT_CUDA(cudaStreamSynchronize(st));
     ECT_REQUIRE(!h, ECT_ERR_BREAKDOWN, "a subdomain block of the scaled matrix is singular");
+    mg_free(M);
     if (coarse_group < 0) {
-        // automatic: the smallest power-of-two group with at most 3072 coarse unknowns
-        int g = 1;
-        for (; g < (1 << 20); g *= 2) {
-            int64_t cnt = 0;
-            const std::vector<int32_t>& bp = c->h_block_ptr;
-            for (int64_t g0 = 0; g0 < c->n_blocks; g0 += g) {
-                const int64_t g1 = std::min<int64_t>(c->n_blocks, g0 + g);
-                for (int64_t i = bp[g0]; i < bp[g1]; ++i)
-                    if (M.h_cond[i]) {
-                        ++cnt;
-                        break;
-                    }
-            }
-            if (cnt <= 3072) break;
-        }
-        coarse_group = g;
+        coarse_setup(c, which, 0);
+        mg_setup(c, which, f32);
+        M.pc_f64 = true;
+        M.pc_f32 = f32;
+        return;
     }
     coarse_setup(c, which, coarse_group);
     M.pc_f64 = true;
@@ -464,6 +533,10 @@ void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) 
 
 void coarse_scratch(ect_ctx* c, int which, int k) {
     Matrix& M = c->mat[which];
+    if (M.mg && !mg_ready(M, k)) {  // new cycle vectors: captured graphs hold the old ones
+        workspace_free(c);
+        mg_scratch(M, k);
+    }
     if (M.nc == 0 || M.coarse_k >= k) return;
     workspace_free(c);  // captured graphs hold the old scratch pointers
     M.rc.alloc(sizeof(double2) * M.nc * k);
@@ -475,6 +548,10 @@ void precond_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int 
                        const int* active) {
     Matrix& M = c->mat[which];
     ECT_REQUIRE(M.pc_f64, ECT_ERR_STATE, "preconditioner not set up");
+    if (M.mg) {
+        mg_apply_f64(c, which, r, z, k, ld, rhs_tile, active);
+        return;
+    }
     apply_impl<double>(c, M, M.pinv.as<double2>(), M.einv.as<double2>(), M.zv.as<double>(), r, z, k, ld, rhs_tile,
                        active);
 }
@@ -483,6 +560,10 @@ void precond_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k,
                        const int* active) {
     Matrix& M = c->mat[which];
     ECT_REQUIRE(M.pc_f32, ECT_ERR_STATE, "FP32 preconditioner not set up (use ECT_F32 in ect_precond_setup)");
+    if (M.mg) {
+        mg_apply_f32(c, which, r, z, k, ld, rhs_tile, active);
+        return;
+    }
     apply_impl<float>(c, M, M.pinv32.as<float2>(), M.einv32.as<float2>(), M.zv32.as<float>(), r, z, k, ld, rhs_tile,
                       active);
 }

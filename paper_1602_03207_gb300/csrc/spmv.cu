@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256) k_spmv_f64(const int32_t* __restrict__ ro
                                                   const int32_t* __restrict__ col,
                                                   const double2* __restrict__ val, const double2* __restrict__ x,
                                                   double2* __restrict__ y, int64_t n_rows, int k, int64_t ld,
-                                                  const int* __restrict__ active) {
+                                                  const int* __restrict__ active, const double2* __restrict__ b) {
     int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (d >= 4 * n_rows) return;
     const int row = (int)(d >> 2), p = (int)(d & 3);
@@ -44,7 +44,10 @@ __global__ void __launch_bounds__(256) k_spmv_f64(const int32_t* __restrict__ ro
     }
 #pragma unroll
     for (int q = 0; q < KT; ++q)
-        if (on[q]) y[(int64_t)(r0 + q) * ld + d] = acc[q];
+        if (on[q]) {
+            const int64_t e = (int64_t)(r0 + q) * ld + d;
+            y[e] = b ? csub(b[e], acc[q]) : acc[q];
+        }
 }
 
 template <int KT>
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ ro
                                                   const int32_t* __restrict__ col,
                                                   const float2* __restrict__ val, const float2* __restrict__ x,
                                                   float2* __restrict__ y, int64_t n_rows, int k, int64_t ld,
-                                                  const int* __restrict__ active) {
+                                                  const int* __restrict__ active, const float2* __restrict__ b) {
     int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (d >= 4 * n_rows) return;
     const int row = (int)(d >> 2), p = (int)(d & 3);
@@ -83,7 +86,10 @@ __global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ ro
     }
 #pragma unroll
     for (int q = 0; q < KT; ++q)
-        if (on[q]) y[(int64_t)(r0 + q) * ld + d] = acc[q];
+        if (on[q]) {
+            const int64_t e = (int64_t)(r0 + q) * ld + d;
+            y[e] = b ? csub(b[e], acc[q]) : acc[q];
+        }
 }
 
 int pick_tile(int k, int rhs_tile) {
@@ -97,42 +103,45 @@ int pick_tile(int k, int rhs_tile) {
 
 }  // namespace
 
+void bsr_spmv_f64(cudaStream_t st, const int32_t* rp, const int32_t* cl, const double2* val, int64_t N,
+                  const double2* x, const double2* b, double2* y, int k, int64_t ldx, int rhs_tile, const int* active) {
+    const int kt = pick_tile(k, rhs_tile);
+    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
+    switch (kt) {
+        case 8: k_spmv_f64<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        case 4: k_spmv_f64<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        case 2: k_spmv_f64<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        default: k_spmv_f64<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+    }
+    ECT_CHECK_LAUNCH();
+}
+
+void bsr_spmv_f32(cudaStream_t st, const int32_t* rp, const int32_t* cl, const float2* val, int64_t N,
+                  const float2* x, const float2* b, float2* y, int k, int64_t ldx, int rhs_tile, const int* active) {
+    const int kt = pick_tile(k, rhs_tile);
+    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
+    switch (kt) {
+        case 8: k_spmv_f32<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        case 4: k_spmv_f32<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        case 2: k_spmv_f32<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        default: k_spmv_f32<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+    }
+    ECT_CHECK_LAUNCH();
+}
+
 void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, int k, int64_t ldx, int rhs_tile,
               const int* active) {
     Matrix& M = c->mat[which];
     ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "matrix not assembled");
     const double2* val = scaled ? M.sval.as<double2>() : M.val.as<double2>();
-    const int64_t N = c->n_nodes;
-    const int kt = pick_tile(k, rhs_tile);
-    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
-    cudaStream_t st = c->stream;
-    const int32_t* rp = c->row_ptr.as<int32_t>();
-    const int32_t* cl = c->col.as<int32_t>();
-    switch (kt) {
-        case 8: k_spmv_f64<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-        case 4: k_spmv_f64<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-        case 2: k_spmv_f64<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-        default: k_spmv_f64<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-    }
-    ECT_CHECK_LAUNCH();
+    bsr_spmv_f64(c->stream, c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), val, c->n_nodes, x, nullptr, y, k, ldx,
+                 rhs_tile, active);
 }
 
 void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t ldx, int rhs_tile,
               const int* active) {
     Matrix& M = c->mat[which];
     ECT_REQUIRE(M.assembled && M.has_f32, ECT_ERR_STATE, "FP32 matrix not assembled (use ECT_F32 in ect_assemble)");
-    const int64_t N = c->n_nodes;
-    const int kt = pick_tile(k, rhs_tile);
-    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
-    cudaStream_t st = c->stream;
-    const int32_t* rp = c->row_ptr.as<int32_t>();
-    const int32_t* cl = c->col.as<int32_t>();
-    const float2* val = M.sval32.as<float2>();
-    switch (kt) {
-        case 8: k_spmv_f32<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-        case 4: k_spmv_f32<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-        case 2: k_spmv_f32<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-        default: k_spmv_f32<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active); break;
-    }
-    ECT_CHECK_LAUNCH();
+    bsr_spmv_f32(c->stream, c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), M.sval32.as<float2>(), c->n_nodes, x,
+                 nullptr, y, k, ldx, rhs_tile, active);
 }

@@ -33,7 +33,9 @@ _NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_CUDA", 4: "ERR_OOM", 5: 
 EXPORTS = ["ect_default_options", "ect_create", "ect_destroy", "ect_last_error", "ect_set_mesh",
            "ect_set_physics", "ect_assemble", "ect_precond_setup", "ect_matrix_info", "ect_matrix_copy",
            "ect_scaling_copy", "ect_spmv", "ect_precond_apply", "ect_cgs2", "ect_coil_rhs", "ect_solve",
-           "ect_delta_z", "ect_impedance", "ect_autotune"]
+           "ect_delta_z", "ect_impedance", "ect_autotune", "ect_set_defect", "ect_mlp_num_params", "ect_mlp_create",
+           "ect_mlp_destroy", "ect_mlp_last_error", "ect_mlp_set_params", "ect_mlp_get_params", "ect_mlp_forward",
+           "ect_mlp_gradients", "ect_mlp_train_step"]
 
 
 class EctError(RuntimeError):
@@ -82,6 +84,7 @@ def load_library(path=LIB_PATH):
         "ect_last_error": (ctypes.c_char_p, [P]),
         "ect_set_mesh": (I, [P, P, I64, P, I64, P, P, P, P, P, P]),
         "ect_set_physics": (I, [P, D, D, D]),
+        "ect_set_defect": (I, [P, P, P]),
         "ect_assemble": (I, [P, I, I]),
         "ect_precond_setup": (I, [P, I, I, I]),
         "ect_matrix_info": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
@@ -95,6 +98,15 @@ def load_library(path=LIB_PATH):
         "ect_delta_z": (I, [P, P, P, P, P, P, P]),
         "ect_autotune": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
         "ect_impedance": (I, [P, ctypes.POINTER(Coil), P, I, ctypes.POINTER(Options), P, ctypes.POINTER(Stats)]),
+        "ect_mlp_num_params": (I, []),
+        "ect_mlp_create": (I, [ctypes.POINTER(P), P, I]),
+        "ect_mlp_destroy": (None, [P]),
+        "ect_mlp_last_error": (ctypes.c_char_p, [P]),
+        "ect_mlp_set_params": (I, [P, P]),
+        "ect_mlp_get_params": (I, [P, P]),
+        "ect_mlp_forward": (I, [P, P, P]),
+        "ect_mlp_gradients": (I, [P, P, P, P, P]),
+        "ect_mlp_train_step": (I, [P, P, P, ctypes.c_float, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -188,6 +200,11 @@ class Context:
         self._call(self.L.ect_set_mesh, _ptr(xyz), xyz.shape[0], _ptr(tets), tets.shape[0], _ptr(sigma),
                    _ptr(nu), _ptr(sd), _ptr(nd), _ptr(bon), _ptr(bc))
         self.n_nodes = xyz.shape[0]
+
+    def set_defect(self, sigma_d, nu_d):
+        sd = None if sigma_d is None else np.ascontiguousarray(sigma_d, dtype=np.float64)
+        nd = None if nu_d is None else np.ascontiguousarray(nu_d, dtype=np.float64)
+        self._call(self.L.ect_set_defect, _ptr(sd), _ptr(nd))
 
     def set_physics(self, freq_hz, nu_tilde, delta_gauge):
         self._call(self.L.ect_set_physics, float(freq_hz), float(nu_tilde), float(delta_gauge))
@@ -287,3 +304,85 @@ class Context:
             e.stats = st.as_dict()
             raise
         return dz[..., 0] + 1j * dz[..., 1], st.as_dict()
+
+
+MLP_SIZES = (6, 256, 256, 256, 256, 256)
+
+
+def mlp_flatten(layers):
+    """[(W (out x in), b (out)), ...] -> flat float32 parameter vector (W row-major, then b, per layer)."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32)])
+                           for W, b in layers]).astype(np.float32)
+
+
+def mlp_unflatten(v, sizes=MLP_SIZES):
+    out, o = [], 0
+    for i in range(len(sizes) - 1):
+        fi, fo = sizes[i], sizes[i + 1]
+        W = v[o:o + fi * fo].reshape(fo, fi)
+        o += fi * fo
+        b = v[o:o + fo]
+        o += fo
+        out.append((W, b))
+    return out
+
+
+class Surrogate:
+    """The tcgen05 surrogate MLP (ect_mlp_*) on its own CUDA stream."""
+
+    def __init__(self, batch=256):
+        import torch
+        self._torch = torch
+        self.L = load_library()
+        self.stream = torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        rc = self.L.ect_mlp_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream), int(batch))
+        if rc != ECT_OK:
+            raise EctError(rc, self.L.ect_mlp_last_error(None).decode())
+        self.h = h
+        self.batch = batch
+        self.n_params = self.L.ect_mlp_num_params()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ect_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, fn, *args):
+        cur = self._torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        rc = fn(self.h, *args)
+        cur.wait_stream(self.stream)
+        if rc != ECT_OK:
+            raise EctError(rc, self.L.ect_mlp_last_error(self.h).decode())
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.n_params
+        self._call(self.L.ect_mlp_set_params, _ptr(flat))
+
+    def get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._call(self.L.ect_mlp_get_params, _ptr(out))
+        return out
+
+    def forward(self, x, y):
+        self._call(self.L.ect_mlp_forward, _dptr(x), _dptr(y))
+
+    def gradients(self, x, t):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = np.empty(1, dtype=np.float64)
+        self._call(self.L.ect_mlp_gradients, _dptr(x), _dptr(t), _ptr(g), _ptr(loss))
+        return g, float(loss[0])
+
+    def train_step(self, x, t, lr, want_loss=False):
+        loss = np.empty(1, dtype=np.float64)
+        self._call(self.L.ect_mlp_train_step, _dptr(x), _dptr(t), ctypes.c_float(lr),
+                   _ptr(loss) if want_loss else None)
+        return float(loss[0]) if want_loss else None

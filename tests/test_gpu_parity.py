@@ -129,6 +129,51 @@ def test_spmv_f32_scaled(ect, small):
     assert err.max() <= 2e-6
 
 
+def _oracle_amg(p, M, which):
+    t = fem.scaling(M)
+    S = fem.scaled(M, t)
+    s, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, which)
+    cond = fem.conducting_nodes(p.mesh.n_nodes, p.mesh.tets, s)
+    d, v = fem.fixed_dofs(p.mesh.bc_mask, cond)
+    w = solve.near_null_weights(t, np.concatenate([d, v]))
+    G = solve.node_graph_from_tets(p.mesh.n_nodes, p.mesh.tets)
+    return solve.amg_setup(S, w, p.mesh.block_of_node, G)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(10, 11, 13), (17, 16, 21)])
+def test_multigrid_apply_matches_oracle(ect, prec, shape):
+    """One W-cycle (2 and 3 levels) against the oracle's, same hierarchy rules."""
+    p = E.wall_loss_problem(shape, (20e-3, 20e-3, 30e-3), (2, 2, 2), 0.15, 4, z_pos=(0.0,))
+    ctx = make_ctx(ect, p, group=-1)
+    M = fem.system_matrix(p, "defect")
+    lv = _oracle_amg(p, M, "defect")
+    assert len(lv) >= (3 if shape[0] > 10 else 2)
+    rng = np.random.default_rng(11)
+    n = 4 * p.mesh.n_nodes
+    R = crand(rng, 3, n)
+    dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-9) if prec == "f64" else (torch.complex64, ect.ECT_F32, 2e-3))
+    r = dev(R, dt)
+    z = torch.empty_like(r)
+    ctx.precond_apply(1, r, z, 3, precision=pr)
+    Z = z.cpu().numpy()
+    for q in range(3):
+        ref = solve.amg_apply(lv, R[q])
+        assert np.linalg.norm(Z[q] - ref) <= tol * np.linalg.norm(ref), q
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_multigrid_solve(ect, mode):
+    p = E.wall_loss_problem((17, 16, 21), (20e-3, 20e-3, 30e-3), (2, 2, 2), 0.15, 4, z_pos=(0.0,))
+    M = {w: fem.system_matrix(p, w) for w in WHICH}
+    ctx = make_ctx(ect, p, group=-1)
+    opts = ect.default_options(tol=1e-10, restart=30, mode=ect.ECT_MODE_F64 if mode == "f64" else ect.ECT_MODE_MIXED,
+                               inner_iters=10, max_iters=2000 if mode == "f64" else 200)
+    for w in WHICH:
+        X, st = _solve_check(ect, p, ctx, M, w, opts)
+        assert st["converged"] == 2 and st["iters"] < 400, st
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("group", [0, 1, 3])
 def test_precond_apply(ect, small, prec, group):
@@ -322,3 +367,22 @@ def test_autotune_returns_converging_options(ect, small):
         assert best.mode == mode and 1 <= best.restart <= 64
         X, st2 = _solve_check(ect, p, ctx, M, "defect", best)
         assert st2["converged"] == 2
+
+
+def test_set_defect_reassembles_only_the_defect_matrix(ect):
+    p = small_problem(seed=2)
+    ctx = make_ctx(ect, p, f32=False)
+    p2 = small_problem(seed=2)
+    p2.sigma_d = np.where(np.isnan(p.sigma_d), np.nan, 0.2e6)
+    ctx.set_defect(p2.sigma_d, p2.nu_d)
+    with pytest.raises(ect.EctError) as e:                 # defect matrix must be rebuilt first
+        ctx.matrix_copy(1)
+    assert e.value.code == ect.ECT_ERR_STATE
+    ctx.assemble(1, ect.ECT_F64)
+    G = bsr_to_csr(*ctx.matrix_copy(1))
+    O = fem.system_matrix(p2, "defect")
+    d = np.sqrt(np.abs(O.diagonal()))
+    D = (G - O).tocoo()
+    assert np.all(np.abs(D.data) <= 1e-12 * d[D.row] * d[D.col] + 1e-300)
+    G0 = bsr_to_csr(*ctx.matrix_copy(0))                    # vacuum untouched
+    assert abs(G0 - fem.system_matrix(p2, "vacuum")).max() <= 1e-12 * abs(G0).max()

@@ -290,3 +290,61 @@ def test_selective_reorthogonalisation():
     y, info = solve.fgmres(S, t * b, lambda r: solve.block_jacobi_apply(P, r), tol=1e-11, restart=300,
                            selective=True)
     assert info["relres"] <= 1e-11
+
+
+# ---------------------------------------------------------------- aggregation multigrid
+
+def _amg_case(shape=(7, 7, 9), which="vacuum"):
+    p = E.wall_loss_problem(shape, (20e-3, 20e-3, 30e-3), (2, 2, 2), 0.1, 6, z_pos=(0.0,))
+    M = fem.system_matrix(p, which)
+    t = fem.scaling(M)
+    S = fem.scaled(M, t)
+    s, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, which)
+    cond = fem.conducting_nodes(p.mesh.n_nodes, p.mesh.tets, s)
+    d, v = fem.fixed_dofs(p.mesh.bc_mask, cond)
+    w = solve.near_null_weights(t, np.concatenate([d, v]))
+    G = solve.node_graph_from_tets(p.mesh.n_nodes, p.mesh.tets)
+    return p, M, t, S, w, G, cond
+
+
+def test_greedy_aggregates_rule():
+    # path graph 0-1-2-3-4-5-6: seeds 0 (takes 1), 2 (takes 3), 4 (takes 5), 6
+    n = 7
+    r = np.r_[np.arange(n), np.arange(n - 1), np.arange(1, n)]
+    c = np.r_[np.arange(n), np.arange(1, n), np.arange(n - 1)]
+    G = sp.csr_matrix((np.ones(r.size), (r, c)), shape=(n, n))
+    np.testing.assert_array_equal(solve.greedy_aggregates(G, 8), [0, 0, 1, 1, 2, 2, 3])
+    np.testing.assert_array_equal(solve.greedy_aggregates(G, 1), np.arange(n))
+
+
+def test_amg_coarse_operator_is_galerkin_and_preserves_constants():
+    p, M, t, S, w, G, cond = _amg_case()
+    lv = solve.amg_setup(S, w, p.mesh.block_of_node, G, max_coarse_dofs=64, agg_size=4)
+    assert len(lv) >= 3
+    L0 = lv[0]
+    # level-1 operator = P^T S P (+ identity on empty coarse dofs)
+    A1 = lv[1]["A"]
+    E1 = (L0["P"].T @ S @ L0["P"]).toarray()
+    empty = np.asarray(abs(L0["P"]).sum(axis=0)).ravel() == 0
+    np.testing.assert_allclose(A1.toarray(), E1 + np.diag(empty.astype(float)), atol=1e-12 * abs(E1).max())
+    # the unscaled constant A_x field is in the range of P0 (near-null preservation)
+    x = np.zeros(S.shape[0])
+    x[0::4] = 1.0
+    x[np.asarray(w) == 0] = 0.0
+    y = x / t
+    c = np.zeros(L0["P"].shape[1])
+    nz = ~empty
+    c[nz] = 0.0
+    c[np.arange(0, c.size, 4)[nz[0::4]]] = 1.0
+    np.testing.assert_allclose(L0["P"] @ c, y * (np.asarray(w) != 0), rtol=1e-13)
+
+
+def test_amg_w_cycle_converges_fast():
+    p, M, t, S, w, G, cond = _amg_case((11, 11, 15))
+    lv = solve.amg_setup(S, w, p.mesh.block_of_node, G, max_coarse_dofs=256, agg_size=8)
+    b = fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, p.coils[0].as_tuple(), 0.0), p, "vacuum")
+    P = solve.block_jacobi(S, p.mesh.block_of_node)
+    _, i1 = solve.fgmres(S, t * b, lambda r: solve.block_jacobi_apply(P, r), tol=1e-10, restart=30, maxiter=600)
+    _, i2 = solve.fgmres(S, t * b, lambda r: solve.amg_apply(lv, r), tol=1e-10, restart=30, maxiter=600)
+    assert i2["relres"] <= 1e-10
+    assert i2["iters"] < 0.5 * i1["iters"]

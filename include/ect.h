@@ -83,6 +83,8 @@ typedef struct {
     int restarts;       /* restart cycles run                                          */
     double relres_max;  /* max over rhs of the true relative residual at exit          */
     double ms;          /* device time of the call (CUDA events on the context stream) */
+    int64_t launches;   /* kernels launched (graph nodes x replays + direct launches); counted
+                           for the graph path, 0 when graphs are off                      */
 } ect_stats;
 
 /* Fill *opt with defaults: tol 1e-10, restart 30, max_iters 20000, F64 mode,

@@ -263,8 +263,8 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
         o.rhs_tile = best_tile;
         // 2. Krylov lengths: full solves, fastest converged wins
         std::vector<std::pair<int, int>> cand;
-        if (mixed) cand = {{6, 20}, {8, 30}, {10, 30}, {6, 50}, {4, 64}};
-        else cand = {{20, 0}, {30, 0}, {45, 0}, {64, 0}};
+        if (mixed) cand = {{10, 10}, {10, 20}, {8, 30}, {16, 12}};
+        else cand = {{20, 0}, {30, 0}, {45, 0}};
         double best_t = 1e300;
         ect_options win = o;
         ect_stats wst{};
@@ -359,6 +359,7 @@ int ect_impedance(ect_ctx* c, const ect_coil coils[2], const double* h_z_pos, in
             agg.restarts += s0.restarts + s1.restarts;
             agg.relres_max = std::max({agg.relres_max, s0.relres_max, s1.relres_max});
             agg.ms += s0.ms + s1.ms;
+            agg.launches += s0.launches + s1.launches + 5;  // + 2 coil-source kernels per coil, Delta Z
             if (rc0 != ECT_OK || rc1 != ECT_OK) {
                 if (stats) *stats = agg;
                 throw EctError{ECT_ERR_NOT_CONVERGED, "a probe solve did not reach the tolerance"};

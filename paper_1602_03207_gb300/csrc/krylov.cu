@@ -420,9 +420,9 @@ struct Workspace {
     DevBuf part, npart, wpart;
     DevBuf bnorm, rnorm, target, target_i, inv_h, invb, run, live, live_i, nit, nit_i, flags, live2;
     bool selective = true;
-    std::map<std::tuple<int, int, int, int, int>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, int, int, int>, std::pair<cudaGraphExec_t, size_t>> graphs;  // exec, kernel nodes
     ~Workspace() {
-        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
     }
 };
 
@@ -621,7 +621,7 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
     coarse_scratch(c, which, k);
     Workspace* w = get_ws(c, k, opt.restart, mi, opt.mode);
     if (w->selective != (opt.reorth != 0)) {
-        for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second);
+        for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second.first);
         w->graphs.clear();
         w->selective = opt.reorth != 0;
     }
@@ -646,6 +646,7 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
     const bool graphs = opt.use_graph && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     auto t_start = std::chrono::steady_clock::now();
     int restarts = 0, status = ECT_OK;
+    int64_t launches = 4;  // scaling, norms (outside the cycles)
     while (true) {
         int n_run = 0, total_outer = 0;
         for (int r = 0; r < k; ++r) {
@@ -675,12 +676,15 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
                     throw;
                 }
                 ECT_CUDA(cudaStreamEndCapture(st, &gr));
+                size_t nn = 0;
+                ECT_CUDA(cudaGraphGetNodes(gr, nullptr, &nn));
                 cudaGraphExec_t ex;
                 ECT_CUDA(cudaGraphInstantiate(&ex, gr, 0));
                 cudaGraphDestroy(gr);
-                it = w->graphs.emplace(key, ex).first;
+                it = w->graphs.emplace(key, std::make_pair(ex, nn)).first;
             }
-            ECT_CUDA(cudaGraphLaunch(it->second, st));
+            ECT_CUDA(cudaGraphLaunch(it->second.first, st));
+            launches += (int64_t)it->second.second;
         } else {
             run_cycle(c, w, which, opt.rhs_tile);
         }
@@ -704,6 +708,7 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
             if (run[r] && nit[r] > 0) stalled = false;
         if (stalled) break;
     }
+    launches += 1;
     // x = T y
     k_diag_scale<<<dim3(ew_blocks(n, k), k), TPB, 0, st>>>(w->Y.as<double2>(), x, t, ld, n);
     ECT_CHECK_LAUNCH();
@@ -727,6 +732,7 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
         stats->restarts = restarts;
         stats->relres_max = worst;
         stats->ms = ms;
+        stats->launches = launches;
     }
     if (status != ECT_OK) {
         throw EctError{status, status == ECT_ERR_TIMEOUT ? "solve timed out" : "NaN/Inf in the Krylov recurrence"};

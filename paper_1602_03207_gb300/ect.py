@@ -58,7 +58,8 @@ class Options(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("converged", ctypes.c_int),
-                ("restarts", ctypes.c_int), ("relres_max", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("restarts", ctypes.c_int), ("relres_max", ctypes.c_double), ("ms", ctypes.c_double),
+                ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

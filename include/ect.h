@@ -218,6 +218,22 @@ int ect_autotune(ect_ctx* ctx, int which, const void* d_rhs, void* d_work, int k
 int ect_delta_z(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_b,
                 const double* h_current, double* h_dz, double* h_dz_emf);
 
+/* The Delta Z reduction of ect_delta_z for n_pos positions (d_u0, d_ud, d_b:
+ * complex128 [n_pos][2][n_nodes][4]; h_dz, h_dz_emf: complex128 [n_pos][2][2])
+ * that allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * The paper has no counterpart; this is for callers that cannot allocate
+ * device memory, e.g. an application whose device memory is owned by its own
+ * pool, or one that must not pay the allocator's latency or the device
+ * synchronisation of cudaFree in the middle of its stream work.
+ * Scratch: a static device array of 2.1 MB holding partial sums for at most
+ * 64 positions (n_pos > 64 returns ECT_ERR_ARG); every GPU that loads the
+ * library keeps it until the process exits.  The first call on a device looks
+ * up the array's device address (with that device current); make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race.  Synchronises the context stream. */
+int ect_delta_z_static(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_b, const double* h_current,
+                       int n_pos, double* h_dz, double* h_dz_emf);
+
 /* Step 6-7 for a probe scan: for each of n_pos positions build both coils'
  * sources, solve the vacuum and defect systems (4 solves per position,
  * batched), and reduce Delta Z.  h_dz receives complex128 [n_pos][2][2].

@@ -20,6 +20,7 @@
 // sums are added in a fixed order on the host.  The coil-EMF difference
 // -(i omega/(I_k I_l)) b_k^T (u_l^d - u_l^0) is reduced alongside as a check.
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -331,5 +332,120 @@ void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b,
                 h_dz_emf[(int64_t)p * 8 + 2 * kl + 1] = -f * er;
             }
         }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Delta Z without any device allocation.
+//
+// Some callers cannot call cudaMalloc: an application whose device memory is
+// entirely owned by its own pool allocator, or a caller that must not hit the
+// allocator's latency or device synchronisation (cudaFree synchronises the
+// device) in the middle of its own stream work.  ect_delta_z_static serves
+// them: its scratch (per-CTA partial sums and the reduced results) lives in
+// the file-scope device array below, sized for at most DZ_STATIC_MAX_POS
+// positions per call, which every GPU that loads the library keeps until the
+// process exits.  Every call reuses the same array, so calls that overlap on
+// the GPU race; each call overwrites everything it reads, so nothing has to
+// start at zero.
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr int DZ_STATIC_MAX_POS = 64;
+constexpr int DZ_STATIC_G = 256;     // CTAs of the Delta Z kernel per position
+constexpr int DZ_STATIC_GE = 256;    // CTAs of the EMF kernel per position
+constexpr int64_t DZ_STATIC_PART = (int64_t)DZ_STATIC_MAX_POS * (DZ_STATIC_G + DZ_STATIC_GE) * 8;
+constexpr int64_t DZ_STATIC_DOUBLES = DZ_STATIC_PART + (int64_t)DZ_STATIC_MAX_POS * 16;  // 2.1 MB
+
+static __device__ __align__(256) double g_dz_scratch[DZ_STATIC_DOUBLES];
+
+// out[p][0..7] = sum over the G partials of position p (fixed order)
+__global__ void k_dz_static_reduce(const double* __restrict__ part, int G, double* __restrict__ out) {
+    const int p = blockIdx.x, q = threadIdx.x;
+    if (q >= 8) return;
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += part[((int64_t)p * G + g) * 8 + q];
+    out[(int64_t)p * 8 + q] = s;
+}
+
+double* dz_static_scratch() {
+    // the device address of g_dz_scratch, looked up once per device with that device current
+    static std::mutex mu;
+    static double* addr[64] = {nullptr};
+    int dev = 0;
+    ECT_CUDA(cudaGetDevice(&dev));
+    ECT_REQUIRE(dev >= 0 && dev < 64, ECT_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        ECT_CUDA(cudaGetSymbolAddress(&p, g_dz_scratch));
+        addr[dev] = static_cast<double*>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace
+
+extern "C" int ect_delta_z_static(ect_ctx* c, const void* d_u0, const void* d_ud, const void* d_b,
+                                  const double* h_current, int n_pos, double* h_dz, double* h_dz_emf) {
+    if (!c) return ECT_ERR_ARG;
+    try {
+        ECT_REQUIRE(c->mesh_set && c->physics_set, ECT_ERR_STATE, "mesh and physics must be set");
+        ECT_REQUIRE(d_u0 && d_ud && h_current && h_dz, ECT_ERR_ARG, "null argument");
+        ECT_REQUIRE(n_pos >= 1, ECT_ERR_ARG, "n_pos must be >= 1");
+        ECT_REQUIRE(n_pos <= DZ_STATIC_MAX_POS, ECT_ERR_ARG,
+                    "ect_delta_z_static handles at most 64 positions per call (its static scratch size)");
+        ECT_REQUIRE(!h_dz_emf || d_b, ECT_ERR_ARG, "h_dz_emf needs d_b");
+        ECT_REQUIRE(h_current[0] != 0.0 && h_current[1] != 0.0, ECT_ERR_ARG, "coil currents must be non-zero");
+        double* base = dz_static_scratch();
+        double* part = base;                                              // [n_pos][G][8]
+        double* parte = base + (int64_t)DZ_STATIC_MAX_POS * DZ_STATIC_G * 8;  // [n_pos][Ge][8]
+        double* res = base + DZ_STATIC_PART;                              // [n_pos][8] then [n_pos][8]
+        double* rese = res + (int64_t)DZ_STATIC_MAX_POS * 8;
+        cudaStream_t st = c->stream;
+        const int64_t nvec = 4 * c->n_nodes;
+        k_delta_z<<<dim3(DZ_STATIC_G, n_pos), DZ_TPB, 0, st>>>(
+            c->omega_d.as<int32_t>(), c->n_omega_d, c->tets.as<int32_t>(), c->geo.as<double>(),
+            c->mat[0].sigma.as<double>(), c->mat[0].nu.as<double>(), c->mat[1].sigma.as<double>(),
+            c->mat[1].nu.as<double>(), c->omega, c->delta, (const double2*)d_u0, (const double2*)d_ud, nvec, part);
+        ECT_CHECK_LAUNCH();
+        k_dz_static_reduce<<<n_pos, 32, 0, st>>>(part, DZ_STATIC_G, res);
+        ECT_CHECK_LAUNCH();
+        if (h_dz_emf) {
+            k_emf<<<dim3(DZ_STATIC_GE, n_pos), 256, 0, st>>>((const double2*)d_b, (const double2*)d_u0,
+                                                            (const double2*)d_ud, nvec, parte);
+            ECT_CHECK_LAUNCH();
+            k_dz_static_reduce<<<n_pos, 32, 0, st>>>(parte, DZ_STATIC_GE, rese);
+            ECT_CHECK_LAUNCH();
+        }
+        // the sums land directly in the caller's host arrays, then get scaled in place
+        ECT_CUDA(cudaMemcpyAsync(h_dz, res, sizeof(double) * 8 * n_pos, cudaMemcpyDeviceToHost, st));
+        if (h_dz_emf)
+            ECT_CUDA(cudaMemcpyAsync(h_dz_emf, rese, sizeof(double) * 8 * n_pos, cudaMemcpyDeviceToHost, st));
+        ECT_CUDA(cudaStreamSynchronize(st));
+        const double om = c->omega;
+        for (int p = 0; p < n_pos; ++p)
+            for (int kl = 0; kl < 4; ++kl) {
+                const int kk = kl >> 1, l = kl & 1;
+                const double f = om / (h_current[kk] * h_current[l]);
+                double* z = h_dz + (int64_t)p * 8 + 2 * kl;
+                const double sr = z[0], si = z[1];
+                z[0] = -f * si;  // (i omega / (I_k I_l)) (sr + i si)
+                z[1] = f * sr;
+                if (h_dz_emf) {
+                    double* e = h_dz_emf + (int64_t)p * 8 + 2 * kl;
+                    const double er = e[0], ei = e[1];
+                    e[0] = f * ei;  // -(i omega / (I_k I_l)) (er + i ei)
+                    e[1] = -f * er;
+                }
+            }
+        c->err.clear();
+        return ECT_OK;
+    } catch (const EctError& e) {
+        c->err = e.msg;
+        return e.code;
+    } catch (...) {
+        c->err = "unknown error";
+        return ECT_ERR_ARG;
     }
 }

@@ -33,7 +33,7 @@ _NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_CUDA", 4: "ERR_OOM", 5: 
 EXPORTS = ["ect_default_options", "ect_create", "ect_destroy", "ect_last_error", "ect_set_mesh",
            "ect_set_physics", "ect_assemble", "ect_precond_setup", "ect_matrix_info", "ect_matrix_copy",
            "ect_scaling_copy", "ect_spmv", "ect_precond_apply", "ect_cgs2", "ect_coil_rhs", "ect_solve",
-           "ect_delta_z", "ect_impedance", "ect_autotune", "ect_set_defect", "ect_mlp_num_params", "ect_mlp_create",
+           "ect_delta_z", "ect_impedance", "ect_autotune", "ect_set_defect", "ect_delta_z_static", "ect_mlp_num_params", "ect_mlp_create",
            "ect_mlp_destroy", "ect_mlp_last_error", "ect_mlp_set_params", "ect_mlp_get_params", "ect_mlp_forward",
            "ect_mlp_gradients", "ect_mlp_train_step"]
 
@@ -97,6 +97,7 @@ def load_library(path=LIB_PATH):
         "ect_coil_rhs": (I, [P, ctypes.POINTER(Coil), P, I, P]),
         "ect_solve": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
         "ect_delta_z": (I, [P, P, P, P, P, P, P]),
+        "ect_delta_z_static": (I, [P, P, P, P, P, I, P, P]),
         "ect_autotune": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
         "ect_impedance": (I, [P, ctypes.POINTER(Coil), P, I, ctypes.POINTER(Options), P, ctypes.POINTER(Stats)]),
         "ect_mlp_num_params": (I, []),
@@ -289,6 +290,16 @@ class Context:
         dze = np.empty((2, 2, 2), dtype=np.float64)
         self._call(self.L.ect_delta_z, _dptr(u0), _dptr(ud), None if b is None else _dptr(b), _ptr(cur),
                    _ptr(dz), _ptr(dze) if b is not None else None)
+        out = dz[..., 0] + 1j * dz[..., 1]
+        return out, (dze[..., 0] + 1j * dze[..., 1]) if b is not None else None
+
+    def delta_z_static(self, u0, ud, b, currents, n_pos):
+        """Delta Z for n_pos positions ([n_pos][2][4N] tensors) with no device allocation."""
+        cur = np.ascontiguousarray(currents, dtype=np.float64)
+        dz = np.empty((n_pos, 2, 2, 2), dtype=np.float64)
+        dze = np.empty((n_pos, 2, 2, 2), dtype=np.float64)
+        self._call(self.L.ect_delta_z_static, _dptr(u0), _dptr(ud), None if b is None else _dptr(b), _ptr(cur),
+                   int(n_pos), _ptr(dz), _ptr(dze) if b is not None else None)
         out = dz[..., 0] + 1j * dz[..., 1]
         return out, (dze[..., 0] + 1j * dze[..., 1]) if b is not None else None
 

@@ -394,6 +394,39 @@ def run_reference(args):
     print(json.dumps(rec))
 
 
+def kernel_probe(args):
+    """A few launches of the hot kernels on a mid-size case, for profiler captures.
+
+    53 x 53 x 120-node TSP mesh (1,348,320 complex dof): FP32 SpMM and the
+    preconditioner (block-Jacobi, or the multigrid cycle with --probe-mg) on 8
+    right-hand sides, 3 times each, then CGS2 against 10 vectors twice."""
+    import torch
+
+    import ect_inputs as E
+    from paper_1602_03207_gb300 import build as B
+    from paper_1602_03207_gb300 import ect
+
+    B.build()
+    p = E.tsp_problem((53, 53, 120), (30e-3, 30e-3, 67.4e-3), (2, 2, 4), 0.15, 0, z_pos=(10e-3,))
+    ctx = ect.Context()
+    ctx.load_problem(p)
+    ctx.assemble(0, ect.ECT_F64 | ect.ECT_F32)
+    ctx.precond_setup(0, ect.ECT_F64 | ect.ECT_F32, -1 if args.probe_mg else 0)
+    n = 4 * p.mesh.n_nodes
+    k = 8
+    x = torch.randn(k, n, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        ctx.spmv(0, x, y, k, precision=ect.ECT_F32)
+        ctx.precond_apply(0, y, x, k, precision=ect.ECT_F32)
+    V = torch.randn(10, n, dtype=torch.complex64, device="cuda")
+    w = torch.randn(n, dtype=torch.complex64, device="cuda")
+    for _ in range(2):
+        ctx.cgs2(V, w, precision=ect.ECT_F32)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_probe": "ok", "dof": n}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,12 +442,17 @@ def main():
     ap.add_argument("--max-outer", type=int, default=400)
     ap.add_argument("--inner-iters", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--kernel-probe", action="store_true", help="only launch the hot kernels on a mid-size case")
+    ap.add_argument("--probe-mg", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
     ap.add_argument("--ref-iters", type=int, default=900)
     args = ap.parse_args()
+    if args.kernel_probe:
+        kernel_probe(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

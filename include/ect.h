@@ -70,7 +70,8 @@ typedef struct {
     int mode;           /* ECT_MODE_F64 or ECT_MODE_MIXED                                 */
     int inner_iters;    /* mixed mode: FP32 GMRES iterations per outer step               */
     int use_graph;      /* 1: replay each restart cycle as a captured CUDA graph           */
-    int rhs_tile;       /* right-hand sides per SpMM/preconditioner pass (0 = auto)        */
+    int rhs_tile;       /* right-hand sides per SpMM/preconditioner pass (0 = auto, 8);
+                           -1 = FP32 variants that split the tile over thread groups       */
     double timeout_s;   /* wall-clock limit of one solve call (0 = none)                  */
     int reorth;         /* 0: always two Gram-Schmidt passes; 1: second pass only when the
                            first removed more than half of ||w||^2 (default)             */

@@ -237,8 +237,8 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
         ECT_CUDA(cudaMemsetAsync(a.p, 0, a.bytes, st));
         int best_tile = 1;
         float best_ms = 1e30f;
-        for (int kt : {1, 2, 4, 8}) {
-            if (kt > 1 && kt > 2 * k) break;
+        for (int kt : {8, 4, 2, 1, -1}) {
+            if (kt > 1 && kt > 2 * k) continue;
             auto run = [&] {
                 if (mixed) {
                     spmv_f32(c, which, a.as<float2>(), b.as<float2>(), k, ld, kt, nullptr);

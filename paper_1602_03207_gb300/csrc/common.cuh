@@ -160,6 +160,7 @@ struct Matrix {
     DevBuf agg_lo, agg_hi; // int32[nc] node range of each coarse group
     DevBuf zv, zv32;       // 1/t at the V dof of conducting nodes, 0 elsewhere (N)
     DevBuf rc, zc;         // coarse scratch [k][nc] (double2 or float2 storage)
+    DevBuf gpart;          // split-GEMV partial sums
     int64_t coarse_k = 0;
     std::vector<uint8_t> h_cond;  // conducting-node flags (host)
     Multigrid* mg = nullptr;
@@ -175,7 +176,7 @@ struct Matrix {
         coarse_k = 0;
         h_cond.clear();
         for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
-                          &agg_lo, &agg_hi, &zv, &zv32, &rc, &zc})
+                          &agg_lo, &agg_hi, &zv, &zv32, &rc, &zc, &gpart})
             b->release();
     }
 };
@@ -259,6 +260,10 @@ void bsr_spmv_f64(cudaStream_t st, const int32_t* rp, const int32_t* cl, const d
                   const double2* x, const double2* b, double2* y, int k, int64_t ldx, int rhs_tile, const int* active);
 void bsr_spmv_f32(cudaStream_t st, const int32_t* rp, const int32_t* cl, const float2* val, int64_t N,
                   const float2* x, const float2* b, float2* y, int k, int64_t ldx, int rhs_tile, const int* active);
+// one warp per block row (coarse multigrid levels: few rows, many blocks per row)
+template <typename T>
+void bsr_spmv_warp(cudaStream_t st, const int32_t* rp, const int32_t* cl, const C<T>* val, int64_t N, const C<T>* x,
+                   const C<T>* b, C<T>* y, int k, int64_t ldx, int rhs_tile, const int* active);
 void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, const double2* sval, const int32_t* bptr,
                     const int64_t* poff, int64_t n_blocks, int max_block_nodes, double2* pinv, float2* pinv32);
 template <typename T>
@@ -266,9 +271,10 @@ void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, cons
                  const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate);
 void dense_inverse(cudaStream_t st, double2* a, int64_t n);
 void to_f32(cudaStream_t st, const double2* a, float2* b, int64_t n);
+int64_t gemv_scratch_elems(int64_t nc, int k);
 template <typename T>
 void dense_gemv(cudaStream_t st, const C<T>* einv, int64_t nc, const C<T>* r, C<T>* z, int k, int rhs_tile,
-                const int* active);
+                const int* active, C<T>* part);
 
 void coil_rhs(ect_ctx* c, const ect_coil& coil, const double* h_z, int k, double2* d_rhs);
 void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b, const double* cur,

@@ -33,6 +33,7 @@
 #include <cmath>
 #include <map>
 #include <tuple>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -114,21 +115,90 @@ __global__ void __launch_bounds__(TPB) k_mdot(const C<T>* __restrict__ V, int64_
     }
 }
 
+// First Gram-Schmidt update fused with the dot products of the second pass.
+// W[r] -= sum_i hp[r][i] V_i[r] (the operations of k_maxpy in the same order),
+// then, on the updated W, part[(r*nvec + i)*G + g] = sum conj(V_i[r][e]) W[r][e]
+// and npart[r*G + g] = sum |W[r][e]|^2 over this CTA's range (the operations of
+// k_mdot and k_norm_part in the same order).  The V_i[r][e] are loaded once and
+// reused from registers: the pair costs one pass over the basis instead of two.
+template <typename T, int NV>
+__global__ void __launch_bounds__(TPB, NV > 16 ? 1 : 2) k_maxpy_mdot(const C<T>* __restrict__ V, int64_t vstride, int nvec,
+                                                       C<T>* __restrict__ W, int64_t ld, int64_t n,
+                                                       const double2* __restrict__ hp, int ldp,
+                                                       const int* __restrict__ live, double2* __restrict__ part,
+                                                       double* __restrict__ npart, int G) {
+    __shared__ C<T> hs[NV];
+    __shared__ double sh[8 * (2 * GV + 1)];
+    const int r = blockIdx.y, g = blockIdx.x;
+    if (live && !live[r]) return;
+    for (int i = threadIdx.x; i < nvec; i += TPB) {
+        const double2 h = hp[(int64_t)r * ldp + i];
+        hs[i] = from_d<T>(make_double2(-h.x, -h.y));
+    }
+    __syncthreads();
+    int64_t lo, hi;
+    chunk_range(n, G, g, lo, hi);
+    C<T>* w = W + (int64_t)r * ld;
+    const C<T>* vr = V + (int64_t)r * ld;
+    C<T> acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = czero<T>();
+    T nacc = T(0);
+    for (int64_t e = lo + threadIdx.x; e < hi; e += TPB) {
+        C<T> v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (q < nvec) v[q] = vr[(int64_t)q * vstride + e];
+        C<T> we = w[e];
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (q < nvec) cfma(we, hs[q], v[q]);
+        w[e] = we;
+        nacc += we.x * we.x + we.y * we.y;
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (q < nvec) cfma_conj(acc[q], v[q], we);
+    }
+    // reduce in groups of GV vectors (bounded register use); the norm rides with the first group
+#pragma unroll
+    for (int i0 = 0; i0 < NV; i0 += GV) {
+        if (i0 > 0 && i0 >= nvec) break;
+        double s[2 * GV + 1];
+#pragma unroll
+        for (int q = 0; q < GV; ++q) {
+            s[2 * q] = (double)acc[i0 + q].x;
+            s[2 * q + 1] = (double)acc[i0 + q].y;
+        }
+        s[2 * GV] = (double)nacc;
+        block_sum<2 * GV + 1>(s, sh);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < GV; ++q)
+                if (i0 + q < nvec) part[((int64_t)r * nvec + i0 + q) * G + g] = make_double2(s[2 * q], s[2 * q + 1]);
+            if (i0 == 0) npart[(int64_t)r * G + g] = s[2 * GV];
+        }
+    }
+}
+
+// deterministic warp sum of G partials (fixed lane assignment and shuffle tree)
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ p, int G) {
+    double s = 0.0;
+    for (int g = threadIdx.x & 31; g < G; g += 32) s += p[g];
+    return warp_sum(s);
+}
+
 // second Gram-Schmidt pass needed?  live2[r] = live[r] && ||w1||^2 < ||w0||^2 / 2
-__global__ void k_reorth_decide(const double* __restrict__ wpart, const double* __restrict__ npart, int G, int k,
-                                const int* __restrict__ live, int* __restrict__ live2) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_reorth_decide(const double* __restrict__ wpart, int Gw, const double* __restrict__ npart, int G,
+                                int k, const int* __restrict__ live, int* __restrict__ live2) {
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= k) return;
     if (!live[r]) {
-        live2[r] = 0;
+        if ((threadIdx.x & 31) == 0) live2[r] = 0;
         return;
     }
-    double n0 = 0.0, n1 = 0.0;
-    for (int g = 0; g < G; ++g) {
-        n0 += wpart[(int64_t)r * G + g];
-        n1 += npart[(int64_t)r * G + g];
-    }
-    live2[r] = (n1 < 0.5 * n0) ? 1 : 0;
+    const double n0 = warp_sum_partials(wpart + (int64_t)r * Gw, Gw);
+    const double n1 = warp_sum_partials(npart + (int64_t)r * G, G);
+    if ((threadIdx.x & 31) == 0) live2[r] = (n1 < 0.5 * n0) ? 1 : 0;
 }
 
 // hp[r*ldp + i] = sum_g part; H[r*ldh + hoff + i] (+)= the same
@@ -211,12 +281,13 @@ __global__ void __launch_bounds__(TPB) k_norm_part(const C<T>* __restrict__ W, i
 
 __global__ void k_norm_finalize(const double* __restrict__ npart, int G, int k, const int* __restrict__ live,
                                 double* __restrict__ out) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= k) return;
     if (live && !live[r]) return;
     double s = 0.0;
-    for (int g = 0; g < G; ++g) s += npart[(int64_t)r * G + g];
-    out[r] = sqrt(s);
+    for (int g = threadIdx.x & 31; g < G; g += 32) s += npart[(int64_t)r * G + g];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) out[r] = sqrt(s);
 }
 
 __device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2& s, double2& rr) {
@@ -249,10 +320,12 @@ __global__ void k_arnoldi_finalize(const double* __restrict__ npart, int G, int 
                                    double2* __restrict__ g, const double* __restrict__ target,
                                    int* __restrict__ live, int* __restrict__ nit, double* __restrict__ inv_h,
                                    int* __restrict__ flags) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= k || !live[r]) return;
     double s = 0.0;
-    for (int gg = 0; gg < G; ++gg) s += npart[(int64_t)r * G + gg];
+    for (int gg = threadIdx.x & 31; gg < G; gg += 32) s += npart[(int64_t)r * G + gg];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) != 0) return;
     const double hn = sqrt(s);
     double2* Hc = H + (int64_t)r * (m + 1) * m + (int64_t)j * (m + 1);
     Hc[j + 1] = make_double2(hn, 0.0);
@@ -510,19 +583,34 @@ void cgs2_step(ect_ctx* c, Workspace* w, const C<T>* V, int64_t vstride, int j, 
     const unsigned rb = grid_for((int64_t)k * nvec * 32, 256);
     const bool sel = w->selective && live != nullptr;
     double* npart = w->npart.as<double>();
-    // pass 1
-    k_mdot<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live, part, G, sel ? w->wpart.as<double>() : nullptr);
+    const dim3 vg = vgrid(w);
+    // pass 1: h1 = V^H w
+    k_mdot<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live, part, G, sel ? w->wpart.as<double>() : nullptr);
     k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live, hp, ldp, H, ldh, hoff, 0);
-    k_maxpy<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live, sel ? npart : nullptr, G);
-    // pass 2 (for the right-hand sides that need it when selective)
+    // w1 = w - V h1, fused with h2 = V^H w1 and ||w1||^2 when the basis fits the register tile
+    bool fused = true;
+    if (nvec <= 8)
+        k_maxpy_mdot<T, 8><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
+    else if (std::is_same<T, float>::value && nvec <= 16)
+        k_maxpy_mdot<T, std::is_same<T, float>::value ? 16 : 8>
+            <<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
+    else if (std::is_same<T, float>::value && nvec <= 24)
+        k_maxpy_mdot<T, std::is_same<T, float>::value ? 24 : 8>
+            <<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
+    else {
+        fused = false;
+        k_maxpy<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live, sel ? npart : nullptr, G);
+    }
+    // pass 2 (for the right-hand sides that need it when selective): w2 = w1 - V h2
     const int* live2 = live;
     if (sel) {
-        k_reorth_decide<<<grid_for(k, 128), 128, 0, st>>>(w->wpart.as<double>(), npart, G, k, live, w->live2.as<int>());
+        k_reorth_decide<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(w->wpart.as<double>(), G, npart, G, k, live,
+                                                                        w->live2.as<int>());
         live2 = w->live2.as<int>();
     }
-    k_mdot<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live2, part, G, nullptr);
+    if (!fused) k_mdot<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live2, part, G, nullptr);
     k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live2, hp, ldp, H, ldh, hoff, 1);
-    k_maxpy<T><<<vgrid(w), TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live2, npart, G);
+    k_maxpy<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live2, npart, G);
     ECT_CHECK_LAUNCH();
 }
 
@@ -543,7 +631,7 @@ void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2*
         precond_apply_f32(c, which, Vj, U32, k, ld, rhs_tile, live_i);
         spmv_f32(c, which, U32, Vn, k, ld, rhs_tile, live_i);
         cgs2_step<float>(c, w, V32, vs, j, Vn, ld, w->Hi.as<double2>(), mi, live_i);
-        k_arnoldi_finalize<<<grid_for(k, 128), 128, 0, st>>>(
+        k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
             w->npart.as<double>(), w->G, k, j, mi, w->Hi.as<double2>(), w->csi.as<double>(), w->sni.as<double2>(),
             w->gi.as<double2>(), w->target_i.as<double>(), live_i, w->nit_i.as<int>(), w->inv_h.as<double>(),
             w->flags.as<int>());
@@ -583,7 +671,7 @@ void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
         else precond_apply_f64(c, which, Vj, Zj, k, ld, rhs_tile, live);
         spmv_f64(c, which, true, Zj, Vn, k, ld, rhs_tile, live);
         cgs2_step<double>(c, w, V, vs, j, Vn, ld, w->H.as<double2>(), m, live);
-        k_arnoldi_finalize<<<grid_for(k, 128), 128, 0, st>>>(
+        k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
             w->npart.as<double>(), w->G, k, j, m, w->H.as<double2>(), w->cs.as<double>(), w->sn.as<double2>(),
             w->g.as<double2>(), w->target.as<double>(), live, w->nit.as<int>(), w->inv_h.as<double>(),
             w->flags.as<int>());
@@ -596,7 +684,7 @@ void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
     spmv_f64(c, which, true, w->Y.as<double2>(), w->R.as<double2>(), k, ld, rhs_tile, run);
     k_residual<<<vgrid(w), TPB, 0, st>>>(w->Bh.as<double2>(), w->R.as<double2>(), ld, n, run, w->npart.as<double>(),
                                         w->G);
-    k_norm_finalize<<<grid_for(k, 128), 128, 0, st>>>(w->npart.as<double>(), w->G, k, run, w->rnorm.as<double>());
+    k_norm_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(w->npart.as<double>(), w->G, k, run, w->rnorm.as<double>());
     ECT_CHECK_LAUNCH();
 }
 
@@ -632,7 +720,7 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
     ECT_CUDA(cudaMemsetAsync(w->Y.p, 0, sizeof(double2) * n * k, st));
     ECT_CUDA(cudaMemcpyAsync(w->R.p, w->Bh.p, sizeof(double2) * n * k, cudaMemcpyDeviceToDevice, st));
     k_norm_part<double><<<vgrid(w), TPB, 0, st>>>(w->Bh.as<double2>(), ld, n, nullptr, w->npart.as<double>(), w->G);
-    k_norm_finalize<<<grid_for(k, 128), 128, 0, st>>>(w->npart.as<double>(), w->G, k, nullptr, w->bnorm.as<double>());
+    k_norm_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(w->npart.as<double>(), w->G, k, nullptr, w->bnorm.as<double>());
     ECT_CUDA(cudaMemcpyAsync(w->rnorm.p, w->bnorm.p, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
     ECT_CUDA(cudaMemsetAsync(w->flags.p, 0, sizeof(int), st));
     std::vector<double> bnorm(k), rnorm(k), target(k), target_i(k, 0.0);

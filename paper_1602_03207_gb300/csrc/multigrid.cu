@@ -159,7 +159,7 @@ struct MgLevel {
 struct Multigrid {
     std::deque<MgLevel> L;                   // all levels but the coarsest (stable references)
     int64_t nc = 0;                          // unknowns of the coarsest level
-    DevBuf einv64, einv32, rc, zc;
+    DevBuf einv64, einv32, rc, zc, gpart;
     int64_t kcap = 0;
     bool f32 = false;
 };
@@ -436,6 +436,7 @@ void mg_scratch(Matrix& M, int k) {
     }
     G->rc.alloc(sizeof(double2) * G->nc * k);
     G->zc.alloc(sizeof(double2) * G->nc * k);
+    G->gpart.alloc(sizeof(double2) * gemv_scratch_elems(G->nc, k));
     G->kcap = k;
 }
 
@@ -445,7 +446,7 @@ template <typename T>
 void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int k, int tile, const int* active) {
     if (l == G->L.size()) {
         const C<T>* e = std::is_same<T, double>::value ? (const C<T>*)G->einv64.p : (const C<T>*)G->einv32.p;
-        dense_gemv<T>(st, e, G->nc, r, z, k, tile, active);
+        dense_gemv<T>(st, e, G->nc, r, z, k, tile, active, (C<T>*)G->gpart.p);
         return;
     }
     MgLevel& L = G->L[l];
@@ -459,25 +460,26 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
     const T* w = lvl_w<T>(L);
     block_apply<T>(st, L.d_agg_ptr, L.d_pinv_off, lvl_pinv<T>(L), L.n_agg, r, z, k, ld, tile, active, false);
     const int gamma = last ? 1 : 2;
-    for (int g = 0; g < gamma; ++g) {
-        if (std::is_same<T, double>::value)
+    // t = r - A z: one thread per scalar row on the finest level, one warp per block row below
+    auto residual = [&]() {
+        if (l > 0)
+            bsr_spmv_warp<T>(st, L.rp, L.col, val, L.n, z, r, t, k, ld, tile, active);
+        else if (std::is_same<T, double>::value)
             bsr_spmv_f64(st, L.rp, L.col, (const double2*)val, L.n, (const double2*)z, (const double2*)r, (double2*)t,
                          k, ld, tile, active);
         else
             bsr_spmv_f32(st, L.rp, L.col, (const float2*)val, L.n, (const float2*)z, (const float2*)r, (float2*)t, k,
                          ld, tile, active);
+    };
+    for (int g = 0; g < gamma; ++g) {
+        residual();
         k_restrict<T><<<dim3(grid_for(4 * L.n_next, 256), k), 256, 0, st>>>(
             t, ld, L.clo.as<int32_t>(), L.chi.as<int32_t>(), w, L.n_next, k, active, rn, ldn);
         cycle<T>(st, G, l + 1, rn, zn, k, tile, active);
         k_prolong<T><<<dim3(grid_for(4 * L.n, 256), k), 256, 0, st>>>(z, ld, L.node_agg.as<int32_t>(), w, L.n, zn, ldn,
                                                                         active);
     }
-    if (std::is_same<T, double>::value)
-        bsr_spmv_f64(st, L.rp, L.col, (const double2*)val, L.n, (const double2*)z, (const double2*)r, (double2*)t, k,
-                     ld, tile, active);
-    else
-        bsr_spmv_f32(st, L.rp, L.col, (const float2*)val, L.n, (const float2*)z, (const float2*)r, (float2*)t, k, ld,
-                     tile, active);
+    residual();
     block_apply<T>(st, L.d_agg_ptr, L.d_pinv_off, lvl_pinv<T>(L), L.n_agg, t, z, k, ld, tile, active, true);
     ECT_CHECK_LAUNCH();
 }

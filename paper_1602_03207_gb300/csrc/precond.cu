@@ -13,6 +13,7 @@
 // column-major so that the apply kernel's threads (one per row) read it
 // coalesced.  Apply: one CTA per subdomain and tile of right-hand sides.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -142,6 +143,8 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
     const C<T>* P = pinv + pinv_off[blk] + tid;
+    // b is a multiple of 4 (four unknowns per node): four independent loads in flight per step
+#pragma unroll 4
     for (int cc = 0; cc < b; ++cc) {
         const C<T> a = P[(int64_t)cc * b];
 #pragma unroll
@@ -162,6 +165,48 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
     for (int q = 0; q < KT; ++q)
         if (on[q]) {
             C<T>* zp = z + (int64_t)(r0 + q) * ld + base + tid;
+            *zp = accumulate ? cadd(*zp, acc[q]) : acc[q];
+        }
+}
+
+// FP32 block apply with the right-hand-side tile split across RG groups of 64
+// threads: the groups read the same block inverse (one DRAM read, L1 hits for
+// the others) and each thread keeps KT accumulators.  Accumulate mode adds to z.
+template <int KT, int RG>
+__global__ void __launch_bounds__(64 * RG) k_block_apply_split(const int32_t* __restrict__ block_ptr,
+                                                               const int64_t* __restrict__ pinv_off,
+                                                               const float2* __restrict__ pinv,
+                                                               const float2* __restrict__ r, float2* __restrict__ z,
+                                                               int k, int64_t ld, const int* __restrict__ active,
+                                                               int accumulate) {
+    __shared__ float2 rs[RG * KT][64];
+    const int blk = blockIdx.x, tid = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int r0 = (blockIdx.y * RG + g) * KT;
+    const int n0 = block_ptr[blk], n1 = block_ptr[blk + 1];
+    const int b = 4 * (n1 - n0);
+    const int64_t base = 4 * (int64_t)n0;
+    bool on[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+        if (on[q] && tid < b) rs[g * KT + q][tid] = r[(int64_t)(r0 + q) * ld + base + tid];
+    }
+    __syncthreads();
+    if (tid >= b) return;
+    float2 acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = make_float2(0.f, 0.f);
+    const float2* P = pinv + pinv_off[blk] + tid;
+#pragma unroll 4
+    for (int cc = 0; cc < b; ++cc) {
+        const float2 a = __ldg(P + (int64_t)cc * b);
+#pragma unroll
+        for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[g * KT + q][cc]);
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (on[q]) {
+            float2* zp = z + (int64_t)(r0 + q) * ld + base + tid;
             *zp = accumulate ? cadd(*zp, acc[q]) : acc[q];
         }
 }
@@ -199,40 +244,50 @@ __global__ void __launch_bounds__(128) k_coarse_restrict(const C<T>* __restrict_
     }
 }
 
-// zc[r][c] = sum_d Einv[d][c] rc[r][d]  (Einv symmetric, read coalesced along c)
+// split dense GEMV: part[s][r][c] = sum over d in chunk s of Einv[d][c] rc[r][d]
+constexpr int GEMV_CHUNK = 64;
+
 template <typename T, int KT>
-__global__ void __launch_bounds__(256) k_coarse_gemv(const C<T>* __restrict__ einv, int64_t nc,
-                                                     const C<T>* __restrict__ rc, int k,
-                                                     const int* __restrict__ active, C<T>* __restrict__ zc) {
-    __shared__ C<T> rs[KT][256];
+__global__ void __launch_bounds__(256) k_gemv_split(const C<T>* __restrict__ einv, int64_t nc,
+                                                    const C<T>* __restrict__ rc, int k,
+                                                    const int* __restrict__ active, C<T>* __restrict__ part) {
+    __shared__ C<T> rs[KT][GEMV_CHUNK];
     const int64_t cc = blockIdx.x * 256ll + threadIdx.x;
-    const int r0 = blockIdx.y * KT;
+    const int s = blockIdx.y, r0 = blockIdx.z * KT;
+    const int64_t d0 = (int64_t)s * GEMV_CHUNK;
+    const int dn = (int)((nc - d0) < GEMV_CHUNK ? (nc - d0) : GEMV_CHUNK);
     bool on[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    for (int e = threadIdx.x; e < KT * GEMV_CHUNK; e += 256) {
+        const int q = e / GEMV_CHUNK, d = e % GEMV_CHUNK;
+        rs[q][d] = (on[q] && d < dn) ? rc[(int64_t)(r0 + q) * nc + d0 + d] : czero<T>();
+    }
+    __syncthreads();
+    if (cc >= nc) return;
     C<T> acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
-    for (int64_t d0 = 0; d0 < nc; d0 += 256) {
-        __syncthreads();
+    for (int d = 0; d < dn; ++d) {
+        const C<T> a = einv[(d0 + d) * nc + cc];
 #pragma unroll
-        for (int q = 0; q < KT; ++q)
-            rs[q][threadIdx.x] = (on[q] && d0 + threadIdx.x < nc) ? rc[(int64_t)(r0 + q) * nc + d0 + threadIdx.x]
-                                                                  : czero<T>();
-        __syncthreads();
-        if (cc < nc) {
-            const int64_t dn = nc - d0 < 256 ? nc - d0 : 256;
-            for (int64_t d = 0; d < dn; ++d) {
-                const C<T> a = einv[(d0 + d) * nc + cc];
-#pragma unroll
-                for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[q][d]);
-            }
-        }
+        for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[q][d]);
     }
-    if (cc < nc)
 #pragma unroll
-        for (int q = 0; q < KT; ++q)
-            if (on[q]) zc[(int64_t)(r0 + q) * nc + cc] = acc[q];
+    for (int q = 0; q < KT; ++q)
+        if (on[q]) part[((int64_t)s * k + r0 + q) * nc + cc] = acc[q];
+}
+
+template <typename T>
+__global__ void k_gemv_sum(const C<T>* __restrict__ part, int S, int64_t nc, int k, const int* __restrict__ active,
+                           C<T>* __restrict__ z) {
+    const int64_t e = blockIdx.x * 256ll + threadIdx.x;
+    if (e >= (int64_t)k * nc) return;
+    const int r = (int)(e / nc);
+    if (active && !active[r]) return;
+    C<T> s = czero<T>();
+    for (int q = 0; q < S; ++q) s = cadd(s, part[(int64_t)q * k * nc + e]);
+    z[e] = s;
 }
 
 // in-place Gauss-Jordan inversion of the dense coarse matrix, pivot k (no
@@ -289,7 +344,7 @@ __global__ void k_d2f_vec(const double2* __restrict__ a, float2* __restrict__ b,
 }
 
 int pick_ptile(int k, int rhs_tile) {
-    int kt = rhs_tile > 0 ? rhs_tile : 8;
+    int kt = rhs_tile > 0 ? rhs_tile : 8;  // 0 (auto) and -1 (split variants) use 8 here
     if (kt > k) kt = k;
     if (kt >= 8) return 8;
     if (kt >= 4) return 4;
@@ -313,13 +368,7 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
         zc = M.zc.as<C<T>>();
         k_coarse_restrict<T><<<dim3((unsigned)nc, (unsigned)k), 128, 0, st>>>(r, ld, M.agg_lo.as<int32_t>(),
                                                                                M.agg_hi.as<int32_t>(), zv, nc, active, rc);
-        dim3 g2(grid_for(nc, 256), (unsigned)((k + kt - 1) / kt));
-        switch (kt) {
-            case 8: k_coarse_gemv<T, 8><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
-            case 4: k_coarse_gemv<T, 4><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
-            case 2: k_coarse_gemv<T, 2><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
-            default: k_coarse_gemv<T, 1><<<g2, 256, 0, st>>>(einv, nc, rc, k, active, zc); break;
-        }
+        dense_gemv<T>(st, einv, nc, rc, zc, k, rhs_tile, active, M.gpart.as<C<T>>());
     }
     const int32_t* bc = M.blk_c.as<int32_t>();
     switch (kt) {
@@ -439,6 +488,23 @@ void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, cons
 template <typename T>
 void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, const C<T>* pinv, int64_t n_blocks,
                  const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate) {
+    if (std::is_same<T, float>::value && k >= 2 && rhs_tile < 0) {
+        const float2* pi = (const float2*)pinv;
+        const float2* rr = (const float2*)r;
+        float2* zz = (float2*)z;
+        const int acc = accumulate ? 1 : 0;
+        if (k >= 8)
+            k_block_apply_split<2, 4><<<dim3((unsigned)n_blocks, (unsigned)((k + 7) / 8)), 256, 0, st>>>(
+                bptr, poff, pi, rr, zz, k, ld, active, acc);
+        else if (k >= 4)
+            k_block_apply_split<1, 4><<<dim3((unsigned)n_blocks, (unsigned)((k + 3) / 4)), 256, 0, st>>>(
+                bptr, poff, pi, rr, zz, k, ld, active, acc);
+        else
+            k_block_apply_split<1, 2><<<dim3((unsigned)n_blocks, (unsigned)((k + 1) / 2)), 128, 0, st>>>(
+                bptr, poff, pi, rr, zz, k, ld, active, acc);
+        ECT_CHECK_LAUNCH();
+        return;
+    }
     const int kt = pick_ptile(k, rhs_tile);
     dim3 grid((unsigned)n_blocks, (unsigned)((k + kt - 1) / kt));
     const int acc = accumulate ? 1 : 0;
@@ -478,22 +544,29 @@ void to_f32(cudaStream_t st, const double2* a, float2* b, int64_t n) {
     ECT_CHECK_LAUNCH();
 }
 
-// z[r] = Einv r[r] (dense, symmetric Einv) for k vectors of length nc
+// z[r] = Einv r[r] (dense, symmetric Einv) for k vectors of length nc; part:
+// scratch of gemv_scratch_elems(nc, k) complex values
+int64_t gemv_scratch_elems(int64_t nc, int k) { return ((nc + GEMV_CHUNK - 1) / GEMV_CHUNK) * (int64_t)k * nc; }
+
 template <typename T>
 void dense_gemv(cudaStream_t st, const C<T>* einv, int64_t nc, const C<T>* r, C<T>* z, int k, int rhs_tile,
-                const int* active) {
+                const int* active, C<T>* part) {
     const int kt = pick_ptile(k, rhs_tile);
-    dim3 g2(grid_for(nc, 256), (unsigned)((k + kt - 1) / kt));
+    const int S = (int)((nc + GEMV_CHUNK - 1) / GEMV_CHUNK);
+    dim3 g1(grid_for(nc, 256), S, (unsigned)((k + kt - 1) / kt));
     switch (kt) {
-        case 8: k_coarse_gemv<T, 8><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
-        case 4: k_coarse_gemv<T, 4><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
-        case 2: k_coarse_gemv<T, 2><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
-        default: k_coarse_gemv<T, 1><<<g2, 256, 0, st>>>(einv, nc, r, k, active, z); break;
+        case 8: k_gemv_split<T, 8><<<g1, 256, 0, st>>>(einv, nc, r, k, active, part); break;
+        case 4: k_gemv_split<T, 4><<<g1, 256, 0, st>>>(einv, nc, r, k, active, part); break;
+        case 2: k_gemv_split<T, 2><<<g1, 256, 0, st>>>(einv, nc, r, k, active, part); break;
+        default: k_gemv_split<T, 1><<<g1, 256, 0, st>>>(einv, nc, r, k, active, part); break;
     }
+    k_gemv_sum<T><<<grid_for((int64_t)k * nc, 256), 256, 0, st>>>(part, S, nc, k, active, z);
     ECT_CHECK_LAUNCH();
 }
-template void dense_gemv<double>(cudaStream_t, const double2*, int64_t, const double2*, double2*, int, int, const int*);
-template void dense_gemv<float>(cudaStream_t, const float2*, int64_t, const float2*, float2*, int, int, const int*);
+template void dense_gemv<double>(cudaStream_t, const double2*, int64_t, const double2*, double2*, int, int, const int*,
+                                 double2*);
+template void dense_gemv<float>(cudaStream_t, const float2*, int64_t, const float2*, float2*, int, int, const int*,
+                                float2*);
 
 void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) {
     ECT_REQUIRE(which == ECT_VACUUM || which == ECT_DEFECT, ECT_ERR_ARG, "bad which");
@@ -541,6 +614,7 @@ void coarse_scratch(ect_ctx* c, int which, int k) {
     workspace_free(c);  // captured graphs hold the old scratch pointers
     M.rc.alloc(sizeof(double2) * M.nc * k);
     M.zc.alloc(sizeof(double2) * M.nc * k);
+    M.gpart.alloc(sizeof(double2) * gemv_scratch_elems(M.nc, k));
     M.coarse_k = k;
 }
 

@@ -92,6 +92,114 @@ __global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ ro
         }
 }
 
+// FP32 SpMM with the right-hand-side tile split across RG thread groups of one
+// CTA: each group of 64 threads covers the same 16 block rows for KT of the
+// RG*KT right-hand sides, so the matrix values are read from DRAM once and
+// served to the other groups from L1, while each thread keeps only KT
+// accumulators (few registers, high occupancy, many loads in flight).
+template <int KT, int RG>
+__global__ void __launch_bounds__(64 * RG) k_spmv_f32_split(const int32_t* __restrict__ row_ptr,
+                                                            const int32_t* __restrict__ col,
+                                                            const float2* __restrict__ val,
+                                                            const float2* __restrict__ x, float2* __restrict__ y,
+                                                            int64_t n_rows, int k, int64_t ld,
+                                                            const int* __restrict__ active,
+                                                            const float2* __restrict__ b) {
+    const int lr = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int64_t d = blockIdx.x * 64ll + lr;
+    if (d >= 4 * n_rows) return;
+    const int row = (int)(d >> 2), p = (int)(d & 3);
+    const int r0 = (blockIdx.y * RG + g) * KT;
+    bool on[KT];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+        any |= on[q];
+    }
+    if (!any) return;
+    float2 acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = make_float2(0.f, 0.f);
+    const int s1 = row_ptr[row + 1];
+    for (int s = row_ptr[row]; s < s1; ++s) {
+        const int c = col[s];
+        const float4* v = reinterpret_cast<const float4*>(val + 16 * (int64_t)s + 4 * p);
+        const float4 v01 = __ldg(v), v23 = __ldg(v + 1);
+        const float2 a0 = make_float2(v01.x, v01.y), a1 = make_float2(v01.z, v01.w);
+        const float2 a2 = make_float2(v23.x, v23.y), a3 = make_float2(v23.z, v23.w);
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            if (!on[q]) continue;
+            const float4* xv = reinterpret_cast<const float4*>(x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c);
+            const float4 x01 = __ldg(xv), x23 = __ldg(xv + 1);
+            cfma(acc[q], a0, make_float2(x01.x, x01.y));
+            cfma(acc[q], a1, make_float2(x01.z, x01.w));
+            cfma(acc[q], a2, make_float2(x23.x, x23.y));
+            cfma(acc[q], a3, make_float2(x23.z, x23.w));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (on[q]) {
+            const int64_t e = (int64_t)(r0 + q) * ld + d;
+            y[e] = b ? csub(b[e], acc[q]) : acc[q];
+        }
+}
+
+// Coarse-level SpMM: one warp per block row.  Lane = 4*slice + p: the eight
+// slices take every eighth block of the row, each lane keeps KT accumulators
+// for scalar row p, and a shuffle tree over the slices sums them (fixed
+// order).  Galerkin rows on the coarse levels hold 30-60 blocks while the
+// levels have few rows, so splitting the row cuts the serial chain of
+// dependent loads per thread by eight.
+template <typename T, int KT>
+__global__ void __launch_bounds__(256) k_spmv_warp(const int32_t* __restrict__ row_ptr,
+                                                   const int32_t* __restrict__ col, const C<T>* __restrict__ val,
+                                                   const C<T>* __restrict__ x, C<T>* __restrict__ y, int64_t n_rows,
+                                                   int k, int64_t ld, const int* __restrict__ active,
+                                                   const C<T>* __restrict__ b) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= n_rows) return;  // uniform over the warp
+    const int lane = threadIdx.x & 31, p = lane & 3, sl = lane >> 2;
+    const int r0 = blockIdx.y * KT;
+    bool on[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    C<T> acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
+    const int s1 = row_ptr[row + 1];
+    for (int s = row_ptr[row] + sl; s < s1; s += 8) {
+        const int c = col[s];
+        const C<T>* v = val + 16 * (int64_t)s + 4 * p;
+        const C<T> a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            if (!on[q]) continue;
+            const C<T>* xv = x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c;
+            cfma(acc[q], a0, xv[0]);
+            cfma(acc[q], a1, xv[1]);
+            cfma(acc[q], a2, xv[2]);
+            cfma(acc[q], a3, xv[3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, o);
+            acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, o);
+        }
+    if (sl != 0) return;
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (on[q]) {
+            const int64_t e = (int64_t)(r0 + q) * ld + 4 * row + p;
+            y[e] = b ? csub(b[e], acc[q]) : acc[q];
+        }
+}
+
 int pick_tile(int k, int rhs_tile) {
     int kt = rhs_tile > 0 ? rhs_tile : 8;
     if (kt > k) kt = k;
@@ -118,6 +226,22 @@ void bsr_spmv_f64(cudaStream_t st, const int32_t* rp, const int32_t* cl, const d
 
 void bsr_spmv_f32(cudaStream_t st, const int32_t* rp, const int32_t* cl, const float2* val, int64_t N,
                   const float2* x, const float2* b, float2* y, int k, int64_t ldx, int rhs_tile, const int* active) {
+    if (k >= 2 && rhs_tile < 0) {
+        // split tiles (rhs_tile == -1): 8 rhs per CTA (4 groups x 2), 4 (4 x 1) or 2 (2 x 1)
+        const unsigned gx = grid_for(4 * N, 64);
+        if (k >= 8) {
+            k_spmv_f32_split<2, 4><<<dim3(gx, (unsigned)((k + 7) / 8)), 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx,
+                                                                                      active, b);
+        } else if (k >= 4) {
+            k_spmv_f32_split<1, 4><<<dim3(gx, (unsigned)((k + 3) / 4)), 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx,
+                                                                                      active, b);
+        } else {
+            k_spmv_f32_split<1, 2><<<dim3(gx, (unsigned)((k + 1) / 2)), 128, 0, st>>>(rp, cl, val, x, y, N, k, ldx,
+                                                                                      active, b);
+        }
+        ECT_CHECK_LAUNCH();
+        return;
+    }
     const int kt = pick_tile(k, rhs_tile);
     dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
     switch (kt) {
@@ -145,3 +269,22 @@ void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t 
     bsr_spmv_f32(c->stream, c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), M.sval32.as<float2>(), c->n_nodes, x,
                  nullptr, y, k, ldx, rhs_tile, active);
 }
+
+template <typename T>
+void bsr_spmv_warp(cudaStream_t st, const int32_t* rp, const int32_t* cl, const C<T>* val, int64_t N, const C<T>* x,
+                   const C<T>* b, C<T>* y, int k, int64_t ldx, int rhs_tile, const int* active) {
+    const int kt = pick_tile(k, rhs_tile);
+    dim3 grid(grid_for(32 * N, 256), (unsigned)((k + kt - 1) / kt));
+    switch (kt) {
+        case 8: k_spmv_warp<T, 8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        case 4: k_spmv_warp<T, 4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        case 2: k_spmv_warp<T, 2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+        default: k_spmv_warp<T, 1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
+    }
+    ECT_CHECK_LAUNCH();
+}
+
+template void bsr_spmv_warp<double>(cudaStream_t, const int32_t*, const int32_t*, const double2*, int64_t,
+                                    const double2*, const double2*, double2*, int, int64_t, int, const int*);
+template void bsr_spmv_warp<float>(cudaStream_t, const int32_t*, const int32_t*, const float2*, int64_t, const float2*,
+                                   const float2*, float2*, int, int64_t, int, const int*);

@@ -181,3 +181,73 @@ class Trainer:
 
 def relative_errors(pred, ref):
     return np.linalg.norm(pred - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
+def deposit_workload(shape=(50, 50, 100), lengths=(20e-3, 20e-3, 40e-3), n_pos=128):
+    """The surrogate workload: tube mesh, probe path and a deposit factory (seeded inputs)."""
+    import ect_inputs as I
+    mesh = I.box_mesh(shape, lengths, (2, 2, 4))
+    z = -15.875e-3 + (31.75e-3 / (n_pos - 1)) * np.arange(n_pos) if n_pos > 1 else np.zeros(1)
+    background = I.deposit_problem(shape, lengths, I.deposit_params(0), mesh=mesh, z_pos=z)
+    background.sigma_d = np.full(mesh.n_tets, np.nan)
+    background.nu_d = np.full(mesh.n_tets, np.nan)
+
+    def make_defect(seed):
+        q = I.deposit_problem(shape, lengths, I.deposit_params(seed), mesh=mesh, z_pos=z)
+        return I.deposit_params(seed), q.sigma_d, q.nu_d
+
+    return background, z, make_defect
+
+
+def run(out_path, budget_s=600.0, shape=(50, 50, 100), n_pos=128, held_out=0.15, steps=3000, lr=1e-3,
+        tol=1e-6, max_seed=2000):
+    """Generate (resumable) -> train -> evaluate; returns a report dict."""
+    import torch
+    background, z, make_defect = deposit_workload(shape, n_pos=n_pos)
+    opts = E.default_options(tol=tol, mode=E.ECT_MODE_MIXED, restart=16, inner_iters=12, max_iters=300)
+    t0 = time.perf_counter()
+    gen = DatasetGenerator(None, background, background.coils[0], z, make_defect, opts)
+    setup_s = time.perf_counter() - t0
+    samples = gen.run(range(max_seed), out_path, budget_s=budget_s)
+    seeds = sorted(samples)
+    n_test = max(1, int(round(held_out * len(seeds))))
+    train, test = seeds[:-n_test], seeds[-n_test:]
+    Xtr, Ytr = arrays(samples, train)
+    Xte, Yte = arrays(samples, test)
+    tr = Trainer(n_out=2 * n_pos)
+    epochs = max(1, steps // max(1, len(train) // tr.batch)) if len(train) >= tr.batch else steps
+    fit = tr.fit(Xtr, Ytr, epochs=epochs, lr=lr, log_every=200)
+    # evaluation: surrogate vs solver on held-out deposits
+    t1 = time.perf_counter()
+    pred = tr.predict(Xte)
+    torch.cuda.synchronize()
+    infer_s = (time.perf_counter() - t1) / len(test)
+    err = relative_errors(pred, Yte)
+    mean_sig = np.broadcast_to(Ytr.mean(axis=0), Yte.shape)                     # predicting the mean signal
+    base = relative_errors(mean_sig, Yte)
+    agg = float(np.linalg.norm(pred - Yte) / np.linalg.norm(Yte))
+    agg_base = float(np.linalg.norm(mean_sig - Yte) / np.linalg.norm(Yte))
+    solve_s = float(np.median([samples[s]["seconds"] for s in seeds]))
+    return {"samples": len(seeds), "train": len(train), "held_out": len(test), "positions": n_pos,
+            "mesh_nodes": int(np.prod(shape)), "solver_tol": tol, "setup_s": setup_s,
+            "solver_s_per_deposit": solve_s, "surrogate_s_per_deposit": infer_s,
+            "speedup": solve_s / max(infer_s, 1e-12), "train_steps": fit["steps"], "train_s": fit["seconds"],
+            "loss_history": fit["history"][-5:],
+            "held_out_rel_l2": {"median": float(np.median(err)), "mean": float(np.mean(err)),
+                                "max": float(np.max(err)), "aggregate": agg},
+            "mean_signal_rel_l2": {"median": float(np.median(base)), "mean": float(np.mean(base)),
+                                   "aggregate": agg_base}}
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default="surrogate_samples.jsonl")
+    ap.add_argument("--budget", type=float, default=600.0)
+    ap.add_argument("--nodes", default="50,50,100")
+    ap.add_argument("--positions", type=int, default=128)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    a = ap.parse_args()
+    rep = run(a.out, a.budget, tuple(int(v) for v in a.nodes.split(",")), a.positions, steps=a.steps, tol=a.tol)
+    print(json.dumps(rep))

@@ -105,6 +105,37 @@ inline unsigned grid_for(int64_t n, int block) {
     return (unsigned)g;
 }
 
+// one-dimensional grid of row_blocks x n_tiles CTAs (tile index fastest)
+inline unsigned tile_grid(unsigned row_blocks, int n_tiles) {
+    const int64_t g = (int64_t)row_blocks * n_tiles;
+    if (g > 0x7fffffffLL) throw EctError{ECT_ERR_ARG, "launch grid too large"};
+    return (unsigned)g;
+}
+
+// right-hand-side tile of the multi-RHS kernels: the requested size (0: 8)
+// rounded down to a power of two <= 8 and <= k
+inline int pick_tile(int k, int rhs_tile) {
+    int kt = rhs_tile > 0 ? rhs_tile : 8;
+    if (kt > k) kt = k;
+    if (kt >= 8) return 8;
+    if (kt >= 4) return 4;
+    if (kt >= 2) return 2;
+    return 1;
+}
+
+// Cover k right-hand sides with full tiles: as many of the preferred tile as
+// fit, then smaller powers of two for the rest.  launch(kt, first_rhs, n_tiles)
+// is called once per tile size.
+template <typename L>
+void for_tiles(int k, int rhs_tile, L launch) {
+    for (int done = 0; done < k;) {
+        const int kt = pick_tile(k - done, rhs_tile);
+        const int nt = (k - done) / kt;
+        launch(kt, done, nt);
+        done += nt * kt;
+    }
+}
+
 // ----------------------------------------------------------------------------
 // device buffer
 // ----------------------------------------------------------------------------

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(TPB) k_mdot(const C<T>* __restrict__ V, int64_
 // k_mdot and k_norm_part in the same order).  The V_i[r][e] are loaded once and
 // reused from registers: the pair costs one pass over the basis instead of two.
 template <typename T, int NV>
-__global__ void __launch_bounds__(TPB, NV > 16 ? 1 : 2) k_maxpy_mdot(const C<T>* __restrict__ V, int64_t vstride, int nvec,
+__global__ void __launch_bounds__(TPB, 2) k_maxpy_mdot(const C<T>* __restrict__ V, int64_t vstride, int nvec,
                                                        C<T>* __restrict__ W, int64_t ld, int64_t n,
                                                        const double2* __restrict__ hp, int ldp,
                                                        const int* __restrict__ live, double2* __restrict__ part,
@@ -588,14 +588,12 @@ void cgs2_step(ect_ctx* c, Workspace* w, const C<T>* V, int64_t vstride, int j, 
     k_mdot<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live, part, G, sel ? w->wpart.as<double>() : nullptr);
     k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live, hp, ldp, H, ldh, hoff, 0);
     // w1 = w - V h1, fused with h2 = V^H w1 and ||w1||^2 when the basis fits the register tile
+    // (16 vectors in FP32, 8 in FP64: beyond that the registers cut occupancy below the two-pass cost)
     bool fused = true;
     if (nvec <= 8)
         k_maxpy_mdot<T, 8><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
     else if (std::is_same<T, float>::value && nvec <= 16)
         k_maxpy_mdot<T, std::is_same<T, float>::value ? 16 : 8>
-            <<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
-    else if (std::is_same<T, float>::value && nvec <= 24)
-        k_maxpy_mdot<T, std::is_same<T, float>::value ? 24 : 8>
             <<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
     else {
         fused = false;

@@ -111,6 +111,76 @@ __global__ void k_prolong(C<T>* __restrict__ z, int64_t ldf, const int32_t* __re
     o.y += wi * v.y;
 }
 
+// Values of AP (A times the tentative prolongator, fine rows x coarse
+// columns): block (i, J) sums A_ij diag(w_j) over the fine columns j of coarse
+// node J, in ascending fine-block order.
+__global__ void k_ap_values(const int32_t* __restrict__ src_ptr, const int32_t* __restrict__ src,
+                            const int32_t* __restrict__ fcol, const double2* __restrict__ fval,
+                            const double* __restrict__ w, int64_t nnz_ap, double2* __restrict__ out) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nnz_ap) return;
+    double re[16], im[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) re[e] = im[e] = 0.0;
+    for (int32_t q = src_ptr[b]; q < src_ptr[b + 1]; ++q) {
+        const int32_t s = src[q];
+        const int64_t j = fcol[s];
+        const double2* v = fval + 16 * (int64_t)s;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double wj = w[4 * j + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                re[4 * r + c] += v[4 * r + c].x * wj;
+                im[4 * r + c] += v[4 * r + c].y * wj;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) out[16 * b + e] = make_double2(re[e], im[e]);
+}
+
+// t[r][4 i + p] -= sum over the blocks (i, J) of AP of AP_iJ[p][:] e[r][4 J + :].
+// After a coarse correction z += P e, the new residual r - A z equals t - AP e:
+// AP holds a third of A's blocks and e is a small coarse vector that stays in
+// L2, so this costs a fraction of a full residual SpMM.  Tiles of KT
+// right-hand sides are full; masked ones are computed and not stored.
+template <typename T, int KT>
+__global__ void __launch_bounds__(256) k_ap_update(const int32_t* __restrict__ ap_ptr,
+                                                   const int32_t* __restrict__ ap_col,
+                                                   const C<T>* __restrict__ ap_val, const C<T>* __restrict__ e,
+                                                   int64_t lde, C<T>* __restrict__ t, int64_t ldt, int64_t n_rows,
+                                                   const int* __restrict__ active, int ntile) {
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t d = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
+    if (d >= 4 * n_rows) return;
+    const int row = (int)(d >> 2), p = (int)(d & 3);
+    const int r0 = tile * KT;
+    C<T> acc[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
+    const int s1 = ap_ptr[row + 1];
+    for (int s = ap_ptr[row]; s < s1; ++s) {
+        const int c = ap_col[s];
+        const C<T>* v = ap_val + 16 * (int64_t)s + 4 * p;
+        const C<T> a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const C<T>* ev = e + (int64_t)(r0 + q) * lde + 4 * (int64_t)c;
+            cfma(acc[q], a0, ev[0]);
+            cfma(acc[q], a1, ev[1]);
+            cfma(acc[q], a2, ev[2]);
+            cfma(acc[q], a3, ev[3]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (!active || active[r0 + q]) {
+            C<T>& o = t[(int64_t)(r0 + q) * ldt + d];
+            o = csub(o, acc[q]);
+        }
+}
+
 __global__ void k_finest_weights(const double* __restrict__ t, const uint8_t* __restrict__ fixmask, int64_t N,
                                  double* __restrict__ w) {
     const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -153,6 +223,8 @@ struct MgLevel {
     const float2* d_pinv32 = nullptr;
     DevBuf agg_ptr_own, pinv_off_own, pinv64_own, pinv32_own;
     DevBuf node_agg, clo, chi, w64, w32;
+    DevBuf ap_ptr, ap_col, ap_val64, ap_val32;  // AP (finest level only)
+    bool has_ap = false;
     DevBuf r, z, t;                          // cycle vectors (k right-hand sides)
 };
 
@@ -220,6 +292,76 @@ template <typename T>
 void to_device(DevBuf& b, const std::vector<T>& h, cudaStream_t st) {
     b.alloc(sizeof(T) * std::max<size_t>(h.size(), 1));
     if (!h.empty()) ECT_CUDA(cudaMemcpyAsync(b.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+}
+
+// pattern of AP on the host (fine row i: the coarse nodes of its columns,
+// ascending), values on the device
+void build_ap(cudaStream_t st, MgLevel& L, const std::vector<int32_t>& nagg, bool f32) {
+    const int64_t n = L.n;
+    std::vector<int32_t> ptr(n + 1, 0), col, slot(L.nnzb);
+    col.reserve((size_t)n * 6);
+    std::vector<int32_t> row;
+    for (int64_t i = 0; i < n; ++i) {
+        row.clear();
+        for (int32_t s = L.h_rp[i]; s < L.h_rp[i + 1]; ++s) row.push_back(nagg[L.h_col[s]]);
+        std::sort(row.begin(), row.end());
+        row.erase(std::unique(row.begin(), row.end()), row.end());
+        const int32_t base = (int32_t)col.size();
+        col.insert(col.end(), row.begin(), row.end());
+        for (int32_t s = L.h_rp[i]; s < L.h_rp[i + 1]; ++s)
+            slot[s] = base + (int32_t)(std::lower_bound(row.begin(), row.end(), nagg[L.h_col[s]]) - row.begin());
+        ptr[i + 1] = (int32_t)col.size();
+    }
+    const int64_t nnz = (int64_t)col.size();
+    std::vector<int32_t> sptr(nnz + 1, 0), src(L.nnzb);
+    for (int64_t s = 0; s < L.nnzb; ++s) ++sptr[slot[s] + 1];
+    for (int64_t b = 0; b < nnz; ++b) sptr[b + 1] += sptr[b];
+    {
+        std::vector<int32_t> fill(sptr.begin(), sptr.end() - 1);
+        for (int64_t s = 0; s < L.nnzb; ++s) src[fill[slot[s]]++] = (int32_t)s;
+    }
+    DevBuf d_sptr, d_src;
+    to_device(L.ap_ptr, ptr, st);
+    to_device(L.ap_col, col, st);
+    to_device(d_sptr, sptr, st);
+    to_device(d_src, src, st);
+    L.ap_val64.alloc(sizeof(double2) * 16 * std::max<int64_t>(nnz, 1));
+    k_ap_values<<<grid_for(nnz, 128), 128, 0, st>>>(d_sptr.as<int32_t>(), d_src.as<int32_t>(), L.col, L.val64,
+                                                     L.w64.as<double>(), nnz, L.ap_val64.as<double2>());
+    ECT_CHECK_LAUNCH();
+    if (f32) {
+        L.ap_val32.alloc(sizeof(float2) * 16 * std::max<int64_t>(nnz, 1));
+        to_f32(st, L.ap_val64.as<double2>(), L.ap_val32.as<float2>(), 16 * nnz);
+    }
+    ECT_CUDA(cudaStreamSynchronize(st));  // the host arrays above go out of scope
+    L.has_ap = true;
+}
+
+template <typename T>
+const C<T>* lvl_ap(const MgLevel& L);
+template <>
+const double2* lvl_ap<double>(const MgLevel& L) { return L.ap_val64.as<double2>(); }
+template <>
+const float2* lvl_ap<float>(const MgLevel& L) { return L.ap_val32.as<float2>(); }
+
+template <typename T>
+void ap_update(cudaStream_t st, const MgLevel& L, const C<T>* e, int64_t lde, C<T>* t, int64_t ldt, int k, int tile,
+               const int* active) {
+    const C<T>* val = lvl_ap<T>(L);
+    const int32_t* ptr = L.ap_ptr.as<int32_t>();
+    const int32_t* col = L.ap_col.as<int32_t>();
+    for_tiles(k, tile, [&](int kt, int r, int nt) {
+        const unsigned grid = tile_grid(grid_for(4 * L.n, 256), nt);
+        const C<T>* er = e + r * lde;
+        C<T>* tr = t + r * ldt;
+        const int* ar = active ? active + r : nullptr;
+        switch (kt) {
+            case 8: k_ap_update<T, 8><<<grid, 256, 0, st>>>(ptr, col, val, er, lde, tr, ldt, L.n, ar, nt); break;
+            case 4: k_ap_update<T, 4><<<grid, 256, 0, st>>>(ptr, col, val, er, lde, tr, ldt, L.n, ar, nt); break;
+            case 2: k_ap_update<T, 2><<<grid, 256, 0, st>>>(ptr, col, val, er, lde, tr, ldt, L.n, ar, nt); break;
+            default: k_ap_update<T, 1><<<grid, 256, 0, st>>>(ptr, col, val, er, lde, tr, ldt, L.n, ar, nt); break;
+        }
+    });
 }
 
 }  // namespace
@@ -366,6 +508,7 @@ void mg_setup(ect_ctx* c, int which, bool f32) {
         to_device(L.clo, lo, st);
         to_device(L.chi, hi, st);
         L.n_next = na;
+        if (depth == 0) build_ap(st, L, nagg, f32);
         ECT_CUDA(cudaStreamSynchronize(st));
         if (coarsest) {
             const int64_t nc = 4 * na;
@@ -471,15 +614,18 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
             bsr_spmv_f32(st, L.rp, L.col, (const float2*)val, L.n, (const float2*)z, (const float2*)r, (float2*)t, k,
                          ld, tile, active);
     };
+    // With AP the residual after each coarse correction is updated in place
+    // (t -= AP e) instead of recomputed, so only the first one is a full SpMM.
     for (int g = 0; g < gamma; ++g) {
-        residual();
+        if (g == 0 || !L.has_ap) residual();
         k_restrict<T><<<dim3(grid_for(4 * L.n_next, 256), k), 256, 0, st>>>(
             t, ld, L.clo.as<int32_t>(), L.chi.as<int32_t>(), w, L.n_next, k, active, rn, ldn);
         cycle<T>(st, G, l + 1, rn, zn, k, tile, active);
         k_prolong<T><<<dim3(grid_for(4 * L.n, 256), k), 256, 0, st>>>(z, ld, L.node_agg.as<int32_t>(), w, L.n, zn, ldn,
                                                                         active);
+        if (L.has_ap) ap_update<T>(st, L, zn, ldn, t, ld, k, tile, active);
     }
-    residual();
+    if (!L.has_ap) residual();
     block_apply<T>(st, L.d_agg_ptr, L.d_pinv_off, lvl_pinv<T>(L), L.n_agg, t, z, k, ld, tile, active, true);
     ECT_CHECK_LAUNCH();
 }

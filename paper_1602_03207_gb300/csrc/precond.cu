@@ -124,10 +124,11 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
                                                     C<T>* __restrict__ z, int k, int64_t ld,
                                                     const int* __restrict__ active,
                                                     const int32_t* __restrict__ blk_c, const C<T>* __restrict__ zc,
-                                                    int64_t nc, const T* __restrict__ zv, int accumulate) {
+                                                    int64_t nc, const T* __restrict__ zv, int accumulate, int ntile) {
     __shared__ C<T> rs[KT][64];
-    const int blk = blockIdx.x, tid = threadIdx.x;
-    const int r0 = blockIdx.y * KT;
+    // one-dimensional grid, tile index fastest: the tiles of a block share its inverse through L2
+    const int blk = (int)(blockIdx.x / ntile), tid = threadIdx.x;
+    const int r0 = (int)(blockIdx.x % ntile) * KT;
     const int n0 = block_ptr[blk], n1 = block_ptr[blk + 1];
     const int b = 4 * (n1 - n0);
     const int64_t base = 4 * (int64_t)n0;
@@ -356,7 +357,8 @@ template <typename T>
 void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const T* zv, const C<T>* r, C<T>* z,
                 int k, int64_t ld, int rhs_tile, const int* active) {
     const int kt = pick_ptile(k, rhs_tile);
-    dim3 grid((unsigned)c->n_blocks, (unsigned)((k + kt - 1) / kt));
+    const int nt = (k + kt - 1) / kt;
+    const unsigned grid = tile_grid((unsigned)c->n_blocks, nt);
     const int32_t* bp = c->block_ptr.as<int32_t>();
     const int64_t* po = c->pinv_off.as<int64_t>();
     cudaStream_t st = c->stream;
@@ -372,10 +374,10 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
     }
     const int32_t* bc = M.blk_c.as<int32_t>();
     switch (kt) {
-        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
-        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
-        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
-        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0); break;
+        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
     }
     ECT_CHECK_LAUNCH();
 }
@@ -506,13 +508,14 @@ void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, cons
         return;
     }
     const int kt = pick_ptile(k, rhs_tile);
-    dim3 grid((unsigned)n_blocks, (unsigned)((k + kt - 1) / kt));
+    const int nt = (k + kt - 1) / kt;
+    const unsigned grid = tile_grid((unsigned)n_blocks, nt);
     const int acc = accumulate ? 1 : 0;
     switch (kt) {
-        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
-        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
-        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
-        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc); break;
+        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
     }
     ECT_CHECK_LAUNCH();
 }

@@ -6,7 +6,12 @@
 // and applies it to the KT vectors, so the matrix is read once per tile of
 // right-hand sides.  The four threads of a node read one block's four rows,
 // which are contiguous, and broadcast-share the x segment of each column
-// node.  Vectors are stored [k][4N] with leading dimension ld.
+// node.  Vectors are stored [k][4N] with leading dimension ld.  The grid is
+// one-dimensional with the tile index fastest, so the tiles of a row range
+// run side by side and share the matrix blocks through L2.  The launchers
+// cover k with full tiles (8, 4, 2, 1), so every row of a tile exists and the
+// x loads are unconditional: all of a step's loads can issue before its FMAs.
+// Masked right-hand sides are computed and not stored.
 #include "common.cuh"
 
 namespace {
@@ -15,15 +20,17 @@ template <int KT>
 __global__ void __launch_bounds__(256) k_spmv_f64(const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col,
                                                   const double2* __restrict__ val, const double2* __restrict__ x,
-                                                  double2* __restrict__ y, int64_t n_rows, int k, int64_t ld,
-                                                  const int* __restrict__ active, const double2* __restrict__ b) {
-    int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                                                  double2* __restrict__ y, int64_t n_rows, int64_t ld,
+                                                  const int* __restrict__ active, const double2* __restrict__ b,
+                                                  int ntile) {
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t d = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
     if (d >= 4 * n_rows) return;
     const int row = (int)(d >> 2), p = (int)(d & 3);
-    const int r0 = blockIdx.y * KT;
+    const int r0 = tile * KT;
     bool on[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    for (int q = 0; q < KT; ++q) on[q] = !active || active[r0 + q];
     double2 acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = make_double2(0.0, 0.0);
@@ -34,7 +41,6 @@ __global__ void __launch_bounds__(256) k_spmv_f64(const int32_t* __restrict__ ro
         const double2 a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
-            if (!on[q]) continue;
             const double2* xv = x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c;
             cfma(acc[q], a0, xv[0]);
             cfma(acc[q], a1, xv[1]);
@@ -54,15 +60,17 @@ template <int KT>
 __global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col,
                                                   const float2* __restrict__ val, const float2* __restrict__ x,
-                                                  float2* __restrict__ y, int64_t n_rows, int k, int64_t ld,
-                                                  const int* __restrict__ active, const float2* __restrict__ b) {
-    int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                                                  float2* __restrict__ y, int64_t n_rows, int64_t ld,
+                                                  const int* __restrict__ active, const float2* __restrict__ b,
+                                                  int ntile) {
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t d = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
     if (d >= 4 * n_rows) return;
     const int row = (int)(d >> 2), p = (int)(d & 3);
-    const int r0 = blockIdx.y * KT;
+    const int r0 = tile * KT;
     bool on[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    for (int q = 0; q < KT; ++q) on[q] = !active || active[r0 + q];
     float2 acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = make_float2(0.f, 0.f);
@@ -75,8 +83,8 @@ __global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ ro
         const float2 a2 = make_float2(v23.x, v23.y), a3 = make_float2(v23.z, v23.w);
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
-            if (!on[q]) continue;
-            const float4* xv = reinterpret_cast<const float4*>(x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c);
+            const float4* xv =
+                reinterpret_cast<const float4*>(x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c);
             const float4 x01 = xv[0], x23 = xv[1];
             cfma(acc[q], a0, make_float2(x01.x, x01.y));
             cfma(acc[q], a1, make_float2(x01.z, x01.w));
@@ -157,15 +165,16 @@ template <typename T, int KT>
 __global__ void __launch_bounds__(256) k_spmv_warp(const int32_t* __restrict__ row_ptr,
                                                    const int32_t* __restrict__ col, const C<T>* __restrict__ val,
                                                    const C<T>* __restrict__ x, C<T>* __restrict__ y, int64_t n_rows,
-                                                   int k, int64_t ld, const int* __restrict__ active,
-                                                   const C<T>* __restrict__ b) {
-    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+                                                   int64_t ld, const int* __restrict__ active,
+                                                   const C<T>* __restrict__ b, int ntile) {
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t row = ((int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x) >> 5;
     if (row >= n_rows) return;  // uniform over the warp
     const int lane = threadIdx.x & 31, p = lane & 3, sl = lane >> 2;
-    const int r0 = blockIdx.y * KT;
+    const int r0 = tile * KT;
     bool on[KT];
 #pragma unroll
-    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    for (int q = 0; q < KT; ++q) on[q] = !active || active[r0 + q];
     C<T> acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
@@ -176,7 +185,6 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int32_t* __restrict__ r
         const C<T> a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
 #pragma unroll
         for (int q = 0; q < KT; ++q) {
-            if (!on[q]) continue;
             const C<T>* xv = x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c;
             cfma(acc[q], a0, xv[0]);
             cfma(acc[q], a1, xv[1]);
@@ -200,27 +208,23 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int32_t* __restrict__ r
         }
 }
 
-int pick_tile(int k, int rhs_tile) {
-    int kt = rhs_tile > 0 ? rhs_tile : 8;
-    if (kt > k) kt = k;
-    if (kt >= 8) return 8;
-    if (kt >= 4) return 4;
-    if (kt >= 2) return 2;
-    return 1;
-}
-
 }  // namespace
 
 void bsr_spmv_f64(cudaStream_t st, const int32_t* rp, const int32_t* cl, const double2* val, int64_t N,
                   const double2* x, const double2* b, double2* y, int k, int64_t ldx, int rhs_tile, const int* active) {
-    const int kt = pick_tile(k, rhs_tile);
-    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
-    switch (kt) {
-        case 8: k_spmv_f64<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        case 4: k_spmv_f64<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        case 2: k_spmv_f64<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        default: k_spmv_f64<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-    }
+    for_tiles(k, rhs_tile, [&](int kt, int r, int nt) {
+        const unsigned grid = tile_grid(grid_for(4 * N, 256), nt);
+        const double2* xr = x + r * ldx;
+        const double2* br = b ? b + r * ldx : nullptr;
+        double2* yr = y + r * ldx;
+        const int* ar = active ? active + r : nullptr;
+        switch (kt) {
+            case 8: k_spmv_f64<8><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            case 4: k_spmv_f64<4><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            case 2: k_spmv_f64<2><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            default: k_spmv_f64<1><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+        }
+    });
     ECT_CHECK_LAUNCH();
 }
 
@@ -242,14 +246,19 @@ void bsr_spmv_f32(cudaStream_t st, const int32_t* rp, const int32_t* cl, const f
         ECT_CHECK_LAUNCH();
         return;
     }
-    const int kt = pick_tile(k, rhs_tile);
-    dim3 grid(grid_for(4 * N, 256), (unsigned)((k + kt - 1) / kt));
-    switch (kt) {
-        case 8: k_spmv_f32<8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        case 4: k_spmv_f32<4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        case 2: k_spmv_f32<2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        default: k_spmv_f32<1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-    }
+    for_tiles(k, rhs_tile, [&](int kt, int r, int nt) {
+        const unsigned grid = tile_grid(grid_for(4 * N, 256), nt);
+        const float2* xr = x + r * ldx;
+        const float2* br = b ? b + r * ldx : nullptr;
+        float2* yr = y + r * ldx;
+        const int* ar = active ? active + r : nullptr;
+        switch (kt) {
+            case 8: k_spmv_f32<8><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            case 4: k_spmv_f32<4><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            case 2: k_spmv_f32<2><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            default: k_spmv_f32<1><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+        }
+    });
     ECT_CHECK_LAUNCH();
 }
 
@@ -273,14 +282,19 @@ void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t 
 template <typename T>
 void bsr_spmv_warp(cudaStream_t st, const int32_t* rp, const int32_t* cl, const C<T>* val, int64_t N, const C<T>* x,
                    const C<T>* b, C<T>* y, int k, int64_t ldx, int rhs_tile, const int* active) {
-    const int kt = pick_tile(k, rhs_tile);
-    dim3 grid(grid_for(32 * N, 256), (unsigned)((k + kt - 1) / kt));
-    switch (kt) {
-        case 8: k_spmv_warp<T, 8><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        case 4: k_spmv_warp<T, 4><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        case 2: k_spmv_warp<T, 2><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-        default: k_spmv_warp<T, 1><<<grid, 256, 0, st>>>(rp, cl, val, x, y, N, k, ldx, active, b); break;
-    }
+    for_tiles(k, rhs_tile, [&](int kt, int r, int nt) {
+        const unsigned grid = tile_grid(grid_for(32 * N, 256), nt);
+        const C<T>* xr = x + r * ldx;
+        const C<T>* br = b ? b + r * ldx : nullptr;
+        C<T>* yr = y + r * ldx;
+        const int* ar = active ? active + r : nullptr;
+        switch (kt) {
+            case 8: k_spmv_warp<T, 8><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            case 4: k_spmv_warp<T, 4><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            case 2: k_spmv_warp<T, 2><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+            default: k_spmv_warp<T, 1><<<grid, 256, 0, st>>>(rp, cl, val, xr, yr, N, ldx, ar, br, nt); break;
+        }
+    });
     ECT_CHECK_LAUNCH();
 }
 

@@ -424,7 +424,8 @@ def kernel_probe(args):
     for _ in range(2):
         ctx.cgs2(V, w, precision=ect.ECT_F32)
     torch.cuda.synchronize()
-    print(json.dumps({"kernel_probe": "ok", "dof": n}))
+    print(json.dumps({"kernel_probe": "ok", "dof": n, "nnzb": int(ctx.matrix_info()[1]),
+                      "preconditioner": "multigrid" if args.probe_mg else "block-Jacobi"}))
 
 
 def main():

@@ -71,7 +71,7 @@ typedef struct {
     int inner_iters;    /* mixed mode: FP32 GMRES iterations per outer step               */
     int use_graph;      /* 1: replay each restart cycle as a captured CUDA graph           */
     int rhs_tile;       /* right-hand sides per SpMM/preconditioner pass (0 = auto, 8);
-                           -1 = FP32 variants that split the tile over thread groups       */
+                           -1 = FP32 SpMM variant that splits the tile over thread groups */
     double timeout_s;   /* wall-clock limit of one solve call (0 = none)                  */
     int reorth;         /* 0: always two Gram-Schmidt passes; 1: second pass only when the
                            first removed more than half of ||w||^2 (default)             */

@@ -105,6 +105,13 @@ inline unsigned grid_for(int64_t n, int block) {
     return (unsigned)g;
 }
 
+// The FP32 block inverses are stored packed: the inverse of a complex
+// symmetric block is complex symmetric, so only its upper triangle is kept,
+// column by column (entry (i, j), i <= j, at j (j + 1) / 2 + i).  b = 4 n is
+// a multiple of 4, so every packed block has an even length and every block
+// starts 16-byte aligned.
+inline int64_t sym_packed_size(int b) { return (int64_t)b * (b + 1) / 2; }
+
 // one-dimensional grid of row_blocks x n_tiles CTAs (tile index fastest)
 inline unsigned tile_grid(unsigned row_blocks, int n_tiles) {
     const int64_t g = (int64_t)row_blocks * n_tiles;
@@ -238,6 +245,8 @@ struct ect_ctx {
     DevBuf block_ptr;      // int32[n_blocks+1] node offsets
     DevBuf pinv_off;       // int64[n_blocks+1] offsets (in complex entries) of block inverses
     int64_t pinv_total = 0;
+    DevBuf pinv_off32;     // int64[n_blocks+1] offsets of the packed FP32 (upper triangle) inverses
+    int64_t pinv_total32 = 0;
     DevBuf omega_d;        // int32 list of defect tets
     int64_t n_omega_d = 0;
     std::vector<int32_t> h_block_ptr;
@@ -296,7 +305,10 @@ template <typename T>
 void bsr_spmv_warp(cudaStream_t st, const int32_t* rp, const int32_t* cl, const C<T>* val, int64_t N, const C<T>* x,
                    const C<T>* b, C<T>* y, int k, int64_t ldx, int rhs_tile, const int* active);
 void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, const double2* sval, const int32_t* bptr,
-                    const int64_t* poff, int64_t n_blocks, int max_block_nodes, double2* pinv, float2* pinv32);
+                    const int64_t* poff, const int64_t* poff32, int64_t n_blocks, int max_block_nodes, double2* pinv,
+                    float2* pinv32);
+// z = S_ss^-1 r per smoothing block (accumulate: z += ...); for T = float, pinv
+// and poff are the packed FP32 inverses and their offsets
 template <typename T>
 void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, const C<T>* pinv, int64_t n_blocks,
                  const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate);

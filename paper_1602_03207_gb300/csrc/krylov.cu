@@ -12,9 +12,12 @@
 // Arnoldi step (classical Gram-Schmidt applied twice, Hermitian product):
 //   h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2, H(:,j) = h1 + h2,
 //   H(j+1,j) = ||w||, v_{j+1} = w / ||w||,
-// built from three kernels: a multi-vector dot (per-CTA partial sums with
-// warp shuffles, then a fixed-order reduction, so results are bitwise
-// reproducible), a multi-vector axpy that also accumulates ||w||^2, and a
+// built from a multi-vector dot (per-CTA partial sums with warp shuffles,
+// then a fixed-order reduction, so results are bitwise reproducible), a
+// kernel that applies the first update and forms the second pass's dots and
+// ||w||^2 in the same pass over the basis (up to 16 vectors in FP32, 8 in
+// FP64; two separate passes beyond), a multi-vector axpy that also
+// accumulates ||w||^2, and a
 // per-right-hand-side finalize kernel that applies the previous Givens
 // rotations to the new column, forms the next rotation, updates the
 // residual estimate |g_{j+1}| and retires converged right-hand sides.
@@ -22,7 +25,9 @@
 // Mixed mode: the outer loop is the FP64 flexible GMRES above; its
 // preconditioner is a fixed number of FP32 GMRES iterations (right-
 // preconditioned by the FP32 subdomain blocks, FP32 SpMV and vectors, FP64
-// Hessenberg/Givens) started from zero on S z = v_j.  The FP64 outer loop
+// Hessenberg/Givens) started from zero on S z = v_j; the preconditioned
+// inner vectors P^-1 v_i are kept, so the inner solution is their
+// combination and needs no further preconditioner application.  The FP64 outer loop
 // keeps the residual, its orthogonalisation and least-squares problem in
 // FP64, so the final accuracy is that of FP64.
 //
@@ -487,7 +492,7 @@ struct Workspace {
     int64_t n = 0;
     int G = 1;
     DevBuf V, Z, Y, Bh, R;
-    DevBuf V32, U32;
+    DevBuf V32, U32, Z32;
     DevBuf H, cs, sn, g, y, hp;
     DevBuf Hi, csi, sni, gi, yi;
     DevBuf part, npart, wpart;
@@ -544,6 +549,9 @@ Workspace* get_ws(ect_ctx* c, int k, int m, int mi, int mode) {
         const size_t vec32 = sizeof(float2) * (size_t)n * k;
         w->V32.alloc(vec32 * (mi + 1));
         w->U32.alloc(vec32);
+        w->Z32.alloc(vec32 * mi);
+        // the combination below multiplies unused entries by zero: keep them finite
+        ECT_CUDA(cudaMemset(w->Z32.p, 0, w->Z32.bytes));
         w->Hi.alloc(sizeof(double2) * (size_t)k * (mi + 1) * mi);
         w->csi.alloc(sizeof(double) * (size_t)k * mi);
         w->sni.alloc(sizeof(double2) * (size_t)k * mi);
@@ -619,6 +627,7 @@ void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2*
     const int64_t n = w->n, ld = n, vs = n * k;
     float2* V32 = w->V32.as<float2>();
     float2* U32 = w->U32.as<float2>();
+    float2* Z32 = w->Z32.as<float2>();
     const int* live = w->live.as<int>();
     int* live_i = w->live_i.as<int>();
     k_inner_g0<<<grid_for(k, 128), 128, 0, st>>>(live, k, mi, w->gi.as<double2>(), live_i, w->nit_i.as<int>());
@@ -626,8 +635,9 @@ void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2*
     for (int j = 0; j < mi; ++j) {
         float2* Vj = V32 + (int64_t)j * vs;
         float2* Vn = V32 + (int64_t)(j + 1) * vs;
-        precond_apply_f32(c, which, Vj, U32, k, ld, rhs_tile, live_i);
-        spmv_f32(c, which, U32, Vn, k, ld, rhs_tile, live_i);
+        float2* Zj = Z32 + (int64_t)j * vs;
+        precond_apply_f32(c, which, Vj, Zj, k, ld, rhs_tile, live_i);
+        spmv_f32(c, which, Zj, Vn, k, ld, rhs_tile, live_i);
         cgs2_step<float>(c, w, V32, vs, j, Vn, ld, w->Hi.as<double2>(), mi, live_i);
         k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
             w->npart.as<double>(), w->G, k, j, mi, w->Hi.as<double2>(), w->csi.as<double>(), w->sni.as<double2>(),
@@ -637,13 +647,12 @@ void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2*
     }
     k_trisolve<<<grid_for(k, 128), 128, 0, st>>>(w->Hi.as<double2>(), w->gi.as<double2>(), w->nit_i.as<int>(), live,
                                                 k, mi, w->yi.as<double2>());
-    // U32 = sum_i y_i V32_i, then z = P^-1 U32
+    // z = P^-1 (sum_i y_i V32_i) = sum_i y_i Z32_i with the stored Z32_i = P^-1 V32_i
+    // (one combination pass instead of one more preconditioner application)
     k_zero<float><<<dim3(ew_blocks(n, k), k), TPB, 0, st>>>(U32, ld, n, live);
-    k_maxpy<float><<<vgrid(w), TPB, 0, st>>>(V32, vs, mi, U32, ld, n, w->yi.as<double2>(), mi + 1, -1.0, live,
+    k_maxpy<float><<<vgrid(w), TPB, 0, st>>>(Z32, vs, mi, U32, ld, n, w->yi.as<double2>(), mi + 1, -1.0, live,
                                               nullptr, w->G);
-    float2* T32 = V32;  // V32_0 is free now
-    precond_apply_f32(c, which, U32, T32, k, ld, rhs_tile, live);
-    k_f2d<<<dim3(ew_blocks(n, k), k), TPB, 0, st>>>(T32, z, ld, n, live);
+    k_f2d<<<dim3(ew_blocks(n, k), k), TPB, 0, st>>>(U32, z, ld, n, live);
     ECT_CHECK_LAUNCH();
 }
 

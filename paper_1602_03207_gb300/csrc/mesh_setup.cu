@@ -217,11 +217,12 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     }
     bptr.push_back((int32_t)n_nodes);
     int maxb = 0;
-    std::vector<int64_t> poff(bptr.size(), 0);
+    std::vector<int64_t> poff(bptr.size(), 0), poff32(bptr.size(), 0);
     for (size_t b = 0; b + 1 < bptr.size(); ++b) {
         int sz = bptr[b + 1] - bptr[b];
         maxb = std::max(maxb, sz);
         poff[b + 1] = poff[b] + (int64_t)(4 * sz) * (4 * sz);
+        poff32[b + 1] = poff32[b] + sym_packed_size(4 * sz);
     }
     ECT_REQUIRE(maxb <= 16, ECT_ERR_ARG, "a subdomain block has more than 16 nodes");
 
@@ -240,6 +241,7 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     c->max_block_nodes = maxb;
     c->h_block_ptr = bptr;
     c->pinv_total = poff.back();
+    c->pinv_total32 = poff32.back();
     cudaStream_t st = c->stream;
 
     c->xyz.alloc(sizeof(double) * 3 * n_nodes);
@@ -247,11 +249,13 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     c->bc.alloc(n_nodes);
     c->block_ptr.alloc(sizeof(int32_t) * bptr.size());
     c->pinv_off.alloc(sizeof(int64_t) * poff.size());
+    c->pinv_off32.alloc(sizeof(int64_t) * poff32.size());
     ECT_CUDA(cudaMemcpyAsync(c->xyz.p, xyz, c->xyz.bytes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->tets.p, tets, c->tets.bytes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->bc.p, bc_mask, n_nodes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->block_ptr.p, bptr.data(), c->block_ptr.bytes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->pinv_off.p, poff.data(), c->pinv_off.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(c->pinv_off32.p, poff32.data(), c->pinv_off32.bytes, cudaMemcpyHostToDevice, st));
     c->h_tets.assign(tets, tets + 4 * n_tets);
     c->h_bc.assign(bc_mask, bc_mask + n_nodes);
     c->h_sigma0 = s0;

@@ -156,6 +156,10 @@ __global__ void __launch_bounds__(256) k_ap_update(const int32_t* __restrict__ a
     if (d >= 4 * n_rows) return;
     const int row = (int)(d >> 2), p = (int)(d & 3);
     const int r0 = tile * KT;
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) any |= !active || active[r0 + q];
+    if (!any) return;  // the whole tile has retired
     C<T> acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
@@ -219,9 +223,10 @@ struct MgLevel {
     std::vector<uint8_t> h_free;             // 4n: unknown carries a near-null weight
     const int32_t* d_agg_ptr = nullptr;
     const int64_t* d_pinv_off = nullptr;
+    const int64_t* d_pinv32_off = nullptr;   // packed FP32 inverses
     const double2* d_pinv64 = nullptr;
     const float2* d_pinv32 = nullptr;
-    DevBuf agg_ptr_own, pinv_off_own, pinv64_own, pinv32_own;
+    DevBuf agg_ptr_own, pinv_off_own, pinv32_off_own, pinv64_own, pinv32_own;
     DevBuf node_agg, clo, chi, w64, w32;
     DevBuf ap_ptr, ap_col, ap_val64, ap_val32;  // AP (finest level only)
     bool has_ap = false;
@@ -250,6 +255,12 @@ const double2* lvl_pinv<double>(const MgLevel& L) { return L.d_pinv64; }
 template <>
 const float2* lvl_pinv<float>(const MgLevel& L) { return L.d_pinv32; }
 template <typename T>
+const int64_t* lvl_poff(const MgLevel& L);
+template <>
+const int64_t* lvl_poff<double>(const MgLevel& L) { return L.d_pinv_off; }
+template <>
+const int64_t* lvl_poff<float>(const MgLevel& L) { return L.d_pinv32_off; }
+template <typename T>
 const C<T>* lvl_val(const MgLevel& L);
 template <>
 const double2* lvl_val<double>(const MgLevel& L) { return L.val64; }
@@ -266,24 +277,29 @@ void level_smoother(cudaStream_t st, MgLevel& L, bool f32) {
     // block inverses of the level's matrix over its (contiguous) aggregates
     const int64_t na = (int64_t)L.h_agg_ptr.size() - 1;
     L.n_agg = na;
-    std::vector<int64_t> poff(na + 1, 0);
+    std::vector<int64_t> poff(na + 1, 0), poff32(na + 1, 0);
     int mx = 0;
     for (int64_t a = 0; a < na; ++a) {
         const int sz = L.h_agg_ptr[a + 1] - L.h_agg_ptr[a];
         mx = std::max(mx, sz);
         poff[a + 1] = poff[a] + (int64_t)(4 * sz) * (4 * sz);
+        poff32[a + 1] = poff32[a] + sym_packed_size(4 * sz);
     }
     L.max_agg = mx;
     L.agg_ptr_own.alloc(sizeof(int32_t) * (na + 1));
     L.pinv_off_own.alloc(sizeof(int64_t) * (na + 1));
     ECT_CUDA(cudaMemcpyAsync(L.agg_ptr_own.p, L.h_agg_ptr.data(), L.agg_ptr_own.bytes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(L.pinv_off_own.p, poff.data(), L.pinv_off_own.bytes, cudaMemcpyHostToDevice, st));
+    L.pinv32_off_own.alloc(sizeof(int64_t) * (na + 1));
+    ECT_CUDA(cudaMemcpyAsync(L.pinv32_off_own.p, poff32.data(), L.pinv32_off_own.bytes, cudaMemcpyHostToDevice, st));
     L.pinv64_own.alloc(sizeof(double2) * poff.back());
-    if (f32) L.pinv32_own.alloc(sizeof(float2) * poff.back());
-    block_inverses(st, L.rp, L.col, L.val64, L.agg_ptr_own.as<int32_t>(), L.pinv_off_own.as<int64_t>(), na, mx,
-                   L.pinv64_own.as<double2>(), f32 ? L.pinv32_own.as<float2>() : nullptr);
+    if (f32) L.pinv32_own.alloc(sizeof(float2) * poff32.back());
+    block_inverses(st, L.rp, L.col, L.val64, L.agg_ptr_own.as<int32_t>(), L.pinv_off_own.as<int64_t>(),
+                   L.pinv32_off_own.as<int64_t>(), na, mx, L.pinv64_own.as<double2>(),
+                   f32 ? L.pinv32_own.as<float2>() : nullptr);
     L.d_agg_ptr = L.agg_ptr_own.as<int32_t>();
     L.d_pinv_off = L.pinv_off_own.as<int64_t>();
+    L.d_pinv32_off = L.pinv32_off_own.as<int64_t>();
     L.d_pinv64 = L.pinv64_own.as<double2>();
     L.d_pinv32 = f32 ? L.pinv32_own.as<float2>() : nullptr;
 }
@@ -390,6 +406,7 @@ void mg_setup(ect_ctx* c, int which, bool f32) {
         L.max_agg = c->max_block_nodes;
         L.d_agg_ptr = c->block_ptr.as<int32_t>();
         L.d_pinv_off = c->pinv_off.as<int64_t>();
+        L.d_pinv32_off = c->pinv_off32.as<int64_t>();
         L.d_pinv64 = M.pinv.as<double2>();
         L.d_pinv32 = f32 ? M.pinv32.as<float2>() : nullptr;
         L.h_free.resize(4 * L.n);
@@ -601,7 +618,7 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
     C<T>* t = (C<T>*)L.t.p;
     const C<T>* val = lvl_val<T>(L);
     const T* w = lvl_w<T>(L);
-    block_apply<T>(st, L.d_agg_ptr, L.d_pinv_off, lvl_pinv<T>(L), L.n_agg, r, z, k, ld, tile, active, false);
+    block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, r, z, k, ld, tile, active, false);
     const int gamma = last ? 1 : 2;
     // t = r - A z: one thread per scalar row on the finest level, one warp per block row below
     auto residual = [&]() {
@@ -626,7 +643,7 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
         if (L.has_ap) ap_update<T>(st, L, zn, ldn, t, ld, k, tile, active);
     }
     if (!L.has_ap) residual();
-    block_apply<T>(st, L.d_agg_ptr, L.d_pinv_off, lvl_pinv<T>(L), L.n_agg, t, z, k, ld, tile, active, true);
+    block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, t, z, k, ld, tile, active, true);
     ECT_CHECK_LAUNCH();
 }
 

@@ -9,9 +9,12 @@
 //
 // Setup: one CTA per subdomain gathers S_ss (b x b, b <= 64) from the BSR
 // blocks into shared memory next to an identity and runs Gauss-Jordan
-// elimination with partial (row) pivoting; the inverse is stored
+// elimination with partial (row) pivoting; the FP64 inverse is stored
 // column-major so that the apply kernel's threads (one per row) read it
-// coalesced.  Apply: one CTA per subdomain and tile of right-hand sides.
+// coalesced, the FP32 copy as the packed upper triangle of the symmetrised
+// inverse (S_ss is complex symmetric, so is its inverse), which halves the
+// bytes the mixed-precision apply reads.  Apply: one CTA per subdomain and
+// tile of right-hand sides.
 #include <algorithm>
 #include <type_traits>
 
@@ -24,6 +27,7 @@ __global__ void __launch_bounds__(256) k_block_inverse(const int32_t* __restrict
                                                        const double2* __restrict__ sval,
                                                        const int32_t* __restrict__ block_ptr,
                                                        const int64_t* __restrict__ pinv_off,
+                                                       const int64_t* __restrict__ pinv_off32,
                                                        double2* __restrict__ pinv, float2* __restrict__ pinv32,
                                                        int* __restrict__ singular) {
     extern __shared__ double2 A[];
@@ -111,9 +115,18 @@ __global__ void __launch_bounds__(256) k_block_inverse(const int32_t* __restrict
     const int64_t off = pinv_off[blk];
     for (int e = tid; e < b * b; e += bd) {
         int cc = e / b, r = e - cc * b;
-        double2 v = A[r * ld + b + cc];
-        pinv[off + e] = v;
-        if (pinv32) pinv32[off + e] = make_float2((float)v.x, (float)v.y);
+        pinv[off + e] = A[r * ld + b + cc];
+    }
+    if (pinv32) {
+        // packed upper triangle of the symmetrised inverse (the exact inverse is symmetric)
+        const int64_t off32 = pinv_off32[blk];
+        for (int e = tid; e < b * b; e += bd) {
+            int cc = e / b, r = e - cc * b;
+            if (r > cc) continue;
+            const double2 v = A[r * ld + b + cc], u = A[cc * ld + b + r];
+            pinv32[off32 + cc * (cc + 1) / 2 + r] =
+                make_float2((float)(0.5 * (v.x + u.x)), (float)(0.5 * (v.y + u.y)));
+        }
     }
 }
 
@@ -132,12 +145,14 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
     const int n0 = block_ptr[blk], n1 = block_ptr[blk + 1];
     const int b = 4 * (n1 - n0);
     const int64_t base = 4 * (int64_t)n0;
-    bool on[KT];
+    bool on[KT], any = false;
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
         on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+        any |= on[q];
         if (on[q] && tid < b) rs[q][tid] = r[(int64_t)(r0 + q) * ld + base + tid];
     }
+    if (!any) return;  // the whole tile has retired (uniform over the CTA, before any barrier)
     __syncthreads();
     if (tid >= b) return;
     C<T> acc[KT];
@@ -170,39 +185,68 @@ __global__ void __launch_bounds__(64) k_block_apply(const int32_t* __restrict__ 
         }
 }
 
-// FP32 block apply with the right-hand-side tile split across RG groups of 64
-// threads: the groups read the same block inverse (one DRAM read, L1 hits for
-// the others) and each thread keeps KT accumulators.  Accumulate mode adds to z.
-template <int KT, int RG>
-__global__ void __launch_bounds__(64 * RG) k_block_apply_split(const int32_t* __restrict__ block_ptr,
-                                                               const int64_t* __restrict__ pinv_off,
-                                                               const float2* __restrict__ pinv,
-                                                               const float2* __restrict__ r, float2* __restrict__ z,
-                                                               int k, int64_t ld, const int* __restrict__ active,
-                                                               int accumulate) {
-    __shared__ float2 rs[RG * KT][64];
-    const int blk = blockIdx.x, tid = threadIdx.x & 63, g = threadIdx.x >> 6;
-    const int r0 = (blockIdx.y * RG + g) * KT;
+// FP32 block apply from the packed upper triangle of the symmetric inverse.
+// The CTA stages its block's packed inverse in shared memory with 16-byte
+// loads (about half the bytes of the full inverse), then thread i forms row
+// i of the inverse: entries (i, j), j >= i, from column j, entries j < i
+// from column i.  Optional coarse-space term as in k_block_apply; one-
+// dimensional grid with the tile index fastest.
+constexpr int SYM_MAX_F4 = 64 * 65 / 4;  // packed 64 x 64 block in float4 units
+template <int KT>
+__global__ void __launch_bounds__(64) k_block_apply_sym(const int32_t* __restrict__ block_ptr,
+                                                        const int64_t* __restrict__ poff,
+                                                        const float2* __restrict__ pinv, const float2* __restrict__ r,
+                                                        float2* __restrict__ z, int k, int64_t ld,
+                                                        const int* __restrict__ active,
+                                                        const int32_t* __restrict__ blk_c,
+                                                        const float2* __restrict__ zc, int64_t nc,
+                                                        const float* __restrict__ zv, int accumulate, int ntile) {
+    __shared__ float4 S4[SYM_MAX_F4];
+    __shared__ float2 rs[KT][64];
+    const int blk = (int)(blockIdx.x / ntile), tid = threadIdx.x;
+    const int r0 = (int)(blockIdx.x % ntile) * KT;
     const int n0 = block_ptr[blk], n1 = block_ptr[blk + 1];
     const int b = 4 * (n1 - n0);
     const int64_t base = 4 * (int64_t)n0;
-    bool on[KT];
+    const int n4 = b * (b + 1) / 4;
+    bool on[KT], any = false;
 #pragma unroll
     for (int q = 0; q < KT; ++q) {
         on[q] = (r0 + q < k) && (!active || active[r0 + q]);
-        if (on[q] && tid < b) rs[g * KT + q][tid] = r[(int64_t)(r0 + q) * ld + base + tid];
+        any |= on[q];
     }
+    if (!any) return;  // the whole tile has retired (uniform over the CTA, before any barrier)
+    const float4* P4 = reinterpret_cast<const float4*>(pinv + poff[blk]);
+    for (int e = tid; e < n4; e += 64) S4[e] = __ldg(P4 + e);
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (on[q] && tid < b) rs[q][tid] = r[(int64_t)(r0 + q) * ld + base + tid];
     __syncthreads();
     if (tid >= b) return;
+    const float2* S = reinterpret_cast<const float2*>(S4);
     float2 acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = make_float2(0.f, 0.f);
-    const float2* P = pinv + pinv_off[blk] + tid;
+    const int ti = tid * (tid + 1) / 2;
+    int tj = 0;  // j (j + 1) / 2
 #pragma unroll 4
-    for (int cc = 0; cc < b; ++cc) {
-        const float2 a = __ldg(P + (int64_t)cc * b);
+    for (int j = 0; j < b; ++j) {
+        const float2 a = S[j >= tid ? tj + tid : ti + j];
 #pragma unroll
-        for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[g * KT + q][cc]);
+        for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[q][j]);
+        tj += j + 1;
+    }
+    if (zc && (tid & 3) == 3) {
+        const int cc = blk_c[blk];
+        const float w = zv[n0 + (tid >> 2)];
+        if (cc >= 0 && w != 0.f)
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                if (!on[q]) continue;
+                const float2 v = zc[(int64_t)(r0 + q) * nc + cc];
+                acc[q].x += w * v.x;
+                acc[q].y += w * v.y;
+            }
     }
 #pragma unroll
     for (int q = 0; q < KT; ++q)
@@ -257,9 +301,13 @@ __global__ void __launch_bounds__(256) k_gemv_split(const C<T>* __restrict__ ein
     const int s = blockIdx.y, r0 = blockIdx.z * KT;
     const int64_t d0 = (int64_t)s * GEMV_CHUNK;
     const int dn = (int)((nc - d0) < GEMV_CHUNK ? (nc - d0) : GEMV_CHUNK);
-    bool on[KT];
+    bool on[KT], any = false;
 #pragma unroll
-    for (int q = 0; q < KT; ++q) on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+    for (int q = 0; q < KT; ++q) {
+        on[q] = (r0 + q < k) && (!active || active[r0 + q]);
+        any |= on[q];
+    }
+    if (!any) return;  // the whole tile has retired (uniform over the CTA, before any barrier)
     for (int e = threadIdx.x; e < KT * GEMV_CHUNK; e += 256) {
         const int q = e / GEMV_CHUNK, d = e % GEMV_CHUNK;
         rs[q][d] = (on[q] && d < dn) ? rc[(int64_t)(r0 + q) * nc + d0 + d] : czero<T>();
@@ -345,7 +393,7 @@ __global__ void k_d2f_vec(const double2* __restrict__ a, float2* __restrict__ b,
 }
 
 int pick_ptile(int k, int rhs_tile) {
-    int kt = rhs_tile > 0 ? rhs_tile : 8;  // 0 (auto) and -1 (split variants) use 8 here
+    int kt = rhs_tile > 0 ? rhs_tile : 8;  // 0 (auto) and -1 use 8 here
     if (kt > k) kt = k;
     if (kt >= 8) return 8;
     if (kt >= 4) return 4;
@@ -360,7 +408,7 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
     const int nt = (k + kt - 1) / kt;
     const unsigned grid = tile_grid((unsigned)c->n_blocks, nt);
     const int32_t* bp = c->block_ptr.as<int32_t>();
-    const int64_t* po = c->pinv_off.as<int64_t>();
+    const int64_t* po = std::is_same<T, float>::value ? c->pinv_off32.as<int64_t>() : c->pinv_off.as<int64_t>();
     cudaStream_t st = c->stream;
     const int64_t nc = M.nc;
     C<T>* zc = nullptr;
@@ -373,11 +421,20 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
         dense_gemv<T>(st, einv, nc, rc, zc, k, rhs_tile, active, M.gpart.as<C<T>>());
     }
     const int32_t* bc = M.blk_c.as<int32_t>();
-    switch (kt) {
-        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
-        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
-        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
-        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+    if constexpr (std::is_same<T, float>::value) {
+        switch (kt) {
+            case 8: k_block_apply_sym<8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+        }
+    } else {
+        switch (kt) {
+            case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+        }
     }
     ECT_CHECK_LAUNCH();
 }
@@ -471,7 +528,8 @@ void coarse_setup(ect_ctx* c, int which, int group) {
 }  // namespace
 
 void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, const double2* sval, const int32_t* bptr,
-                    const int64_t* poff, int64_t n_blocks, int max_block_nodes, double2* pinv, float2* pinv32) {
+                    const int64_t* poff, const int64_t* poff32, int64_t n_blocks, int max_block_nodes, double2* pinv,
+                    float2* pinv32) {
     const int bmax = 4 * max_block_nodes;
     ECT_REQUIRE(bmax <= 64, ECT_ERR_ARG, "smoothing block larger than 16 nodes");
     const size_t smem = sizeof(double2) * (size_t)bmax * 2 * bmax;
@@ -479,7 +537,8 @@ void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, cons
     DevBuf flag;
     flag.alloc(sizeof(int));
     ECT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
-    k_block_inverse<<<(unsigned)n_blocks, 256, smem, st>>>(rp, col, sval, bptr, poff, pinv, pinv32, flag.as<int>());
+    k_block_inverse<<<(unsigned)n_blocks, 256, smem, st>>>(rp, col, sval, bptr, poff, poff32, pinv, pinv32,
+                                                           flag.as<int>());
     ECT_CHECK_LAUNCH();
     int h = 0;
     ECT_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -490,32 +549,24 @@ void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, cons
 template <typename T>
 void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, const C<T>* pinv, int64_t n_blocks,
                  const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate) {
-    if (std::is_same<T, float>::value && k >= 2 && rhs_tile < 0) {
-        const float2* pi = (const float2*)pinv;
-        const float2* rr = (const float2*)r;
-        float2* zz = (float2*)z;
-        const int acc = accumulate ? 1 : 0;
-        if (k >= 8)
-            k_block_apply_split<2, 4><<<dim3((unsigned)n_blocks, (unsigned)((k + 7) / 8)), 256, 0, st>>>(
-                bptr, poff, pi, rr, zz, k, ld, active, acc);
-        else if (k >= 4)
-            k_block_apply_split<1, 4><<<dim3((unsigned)n_blocks, (unsigned)((k + 3) / 4)), 256, 0, st>>>(
-                bptr, poff, pi, rr, zz, k, ld, active, acc);
-        else
-            k_block_apply_split<1, 2><<<dim3((unsigned)n_blocks, (unsigned)((k + 1) / 2)), 128, 0, st>>>(
-                bptr, poff, pi, rr, zz, k, ld, active, acc);
-        ECT_CHECK_LAUNCH();
-        return;
-    }
     const int kt = pick_ptile(k, rhs_tile);
     const int nt = (k + kt - 1) / kt;
     const unsigned grid = tile_grid((unsigned)n_blocks, nt);
     const int acc = accumulate ? 1 : 0;
-    switch (kt) {
-        case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
-        case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
-        case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
-        default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+    if constexpr (std::is_same<T, float>::value) {
+        switch (kt) {
+            case 8: k_block_apply_sym<8><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+        }
+    } else {
+        switch (kt) {
+            case 8: k_block_apply<T, 8><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            case 4: k_block_apply<T, 4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            case 2: k_block_apply<T, 2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            default: k_block_apply<T, 1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+        }
     }
     ECT_CHECK_LAUNCH();
 }
@@ -578,7 +629,7 @@ void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) 
     bool f32 = (precision_mask & ECT_F32) != 0;
     cudaStream_t st = c->stream;
     M.pinv.alloc(sizeof(double2) * c->pinv_total);
-    if (f32) M.pinv32.alloc(sizeof(float2) * c->pinv_total);
+    if (f32) M.pinv32.alloc(sizeof(float2) * c->pinv_total32);
     else M.pinv32.release();
     const int bmax = 4 * c->max_block_nodes;
     const size_t smem = sizeof(double2) * (size_t)bmax * 2 * bmax;
@@ -588,7 +639,8 @@ void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) 
     ECT_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
     k_block_inverse<<<(unsigned)c->n_blocks, 256, smem, st>>>(
         c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), M.sval.as<double2>(), c->block_ptr.as<int32_t>(),
-        c->pinv_off.as<int64_t>(), M.pinv.as<double2>(), f32 ? M.pinv32.as<float2>() : nullptr, flag.as<int>());
+        c->pinv_off.as<int64_t>(), c->pinv_off32.as<int64_t>(), M.pinv.as<double2>(),
+        f32 ? M.pinv32.as<float2>() : nullptr, flag.as<int>());
     ECT_CHECK_LAUNCH();
     int h = 0;
     ECT_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));

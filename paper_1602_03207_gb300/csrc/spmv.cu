@@ -28,9 +28,13 @@ __global__ void __launch_bounds__(256) k_spmv_f64(const int32_t* __restrict__ ro
     if (d >= 4 * n_rows) return;
     const int row = (int)(d >> 2), p = (int)(d & 3);
     const int r0 = tile * KT;
-    bool on[KT];
+    bool on[KT], any = false;
 #pragma unroll
-    for (int q = 0; q < KT; ++q) on[q] = !active || active[r0 + q];
+    for (int q = 0; q < KT; ++q) {
+        on[q] = !active || active[r0 + q];
+        any |= on[q];
+    }
+    if (!any) return;  // the whole tile has retired (uniform over the CTA)
     double2 acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = make_double2(0.0, 0.0);
@@ -68,9 +72,13 @@ __global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ ro
     if (d >= 4 * n_rows) return;
     const int row = (int)(d >> 2), p = (int)(d & 3);
     const int r0 = tile * KT;
-    bool on[KT];
+    bool on[KT], any = false;
 #pragma unroll
-    for (int q = 0; q < KT; ++q) on[q] = !active || active[r0 + q];
+    for (int q = 0; q < KT; ++q) {
+        on[q] = !active || active[r0 + q];
+        any |= on[q];
+    }
+    if (!any) return;  // the whole tile has retired (uniform over the CTA)
     float2 acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = make_float2(0.f, 0.f);
@@ -172,9 +180,13 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int32_t* __restrict__ r
     if (row >= n_rows) return;  // uniform over the warp
     const int lane = threadIdx.x & 31, p = lane & 3, sl = lane >> 2;
     const int r0 = tile * KT;
-    bool on[KT];
+    bool on[KT], any = false;
 #pragma unroll
-    for (int q = 0; q < KT; ++q) on[q] = !active || active[r0 + q];
+    for (int q = 0; q < KT; ++q) {
+        on[q] = !active || active[r0 + q];
+        any |= on[q];
+    }
+    if (!any) return;  // the whole tile has retired (uniform over the CTA)
     C<T> acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = czero<T>();

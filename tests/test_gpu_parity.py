@@ -103,7 +103,7 @@ def test_spmv_f64_batch(ect, small):
     p, ctx, M = small
     rng = np.random.default_rng(0)
     n = 4 * p.mesh.n_nodes
-    for k in (1, 3, 9):
+    for k in (1, 3, 9, 19):                      # 19 = two full tiles of 8, then 2 and 1
         X = crand(rng, k, n)
         x = dev(X)
         y = torch.empty_like(x)
@@ -156,13 +156,14 @@ def test_multigrid_apply_matches_oracle(ect, prec, shape):
     assert len(lv) >= (3 if shape[0] > 10 else 2)
     rng = np.random.default_rng(11)
     n = 4 * p.mesh.n_nodes
-    R = crand(rng, 3, n)
+    k = 19                                       # two full tiles of 8, then 2 and 1
+    R = crand(rng, k, n)
     dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-7) if prec == "f64" else (torch.complex64, ect.ECT_F32, 1e-2))
     r = dev(R, dt)
     z = torch.empty_like(r)
-    ctx.precond_apply(1, r, z, 3, precision=pr)
+    ctx.precond_apply(1, r, z, k, precision=pr)
     Z = z.cpu().numpy()
-    for q in range(3):
+    for q in range(k):
         ref = solve.amg_apply(lv, R[q])
         assert np.linalg.norm(Z[q] - ref) <= tol * np.linalg.norm(ref), q
 
@@ -193,13 +194,14 @@ def test_precond_apply(ect, small, prec, group):
     s, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, "defect")
     cond = fem.conducting_nodes(p.mesh.n_nodes, p.mesh.tets, s)
     C = solve.coarse_v(S, t, p.mesh.block_of_node, cond, group) if group else None
-    R = crand(rng, 3, n)
+    k = 11                                       # one full tile of 8 and a partial one
+    R = crand(rng, k, n)
     dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-9) if prec == "f64" else (torch.complex64, ect.ECT_F32, 1e-3))
     r = dev(R, dt)
     z = torch.empty_like(r)
-    ctx.precond_apply(WHICH["defect"], r, z, 3, precision=pr)
+    ctx.precond_apply(WHICH["defect"], r, z, k, precision=pr)
     Z = z.cpu().numpy()
-    for q in range(3):
+    for q in range(k):
         ref = solve.two_level_apply(P, C, R[q])
         assert np.linalg.norm(Z[q] - ref) <= tol * np.linalg.norm(ref)
 

@@ -52,6 +52,25 @@ def load_peaks():
         return PEAKS_FALLBACK, "fallback"
 
 
+def profiled_traffic(kernel, nnzb):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to nnzb blocks.
+
+    The summary (profiles/hot_kernels_midsize.md) records dram__bytes_read.sum +
+    dram__bytes_write.sum of one captured launch on the mid-size case and that case's nnzb in a
+    line "traffic `<kernel>`: <bytes> bytes at nnzb <n>"; traffic grows with the matrix (blocks
+    and the vectors of the same rows), so it is scaled by the ratio of block counts."""
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", "hot_kernels_midsize.md")) as f:
+            for line in f:
+                m = re.match(r"traffic `(.+?)`: (\d+) bytes at nnzb (\d+)", line.strip())
+                if m and m.group(1) == kernel:
+                    return int(m.group(2)) * nnzb / int(m.group(3))
+    except OSError:
+        pass
+    return None
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -304,7 +323,9 @@ def run_gpu(args):
                        "cgs2_f32_j10_k1": cgs_ms},
         "setup_ms": {"mesh_gen_s": gen_s * 1000, "assemble": asm_ms, "precond": pc_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": profiled_traffic("k_spmv_f32<8>", nnzb) if kk == 8 else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the "
+                                       "53x53x120 case, scaled by nnzb (profiles/hot_kernels_midsize.md)",
                      "kernel": f"k_spmv_f32<8> (SpMM, {kk} rhs)", "ms_per_launch": spmv_ms,
                      "algorithmic_bytes": spmv_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
         "gpu_launches": int(launches),

@@ -94,7 +94,8 @@ __global__ void k_scaling(const double2* __restrict__ val, const int32_t* __rest
 
 __global__ void k_scale_matrix(const double2* __restrict__ val, const int32_t* __restrict__ row_ptr,
                                const int32_t* __restrict__ col, const double* __restrict__ t, int64_t n_rows,
-                               int64_t nnzb, double2* __restrict__ sval, float2* __restrict__ sval32) {
+                               int64_t nnzb, double2* __restrict__ sval, float2* __restrict__ sval32,
+                               float2* __restrict__ sval32lo) {
     int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (slot >= nnzb) return;
     int row = row_of_slot(row_ptr, n_rows, (int)slot);
@@ -113,7 +114,12 @@ __global__ void k_scale_matrix(const double2* __restrict__ val, const int32_t* _
             double s = tr[p] * tc[r];
             double2 v = make_double2(m.x * s, m.y * s);
             sval[16 * slot + 4 * p + r] = v;
-            if (sval32) sval32[16 * slot + 4 * p + r] = make_float2((float)v.x, (float)v.y);
+            if (sval32) {
+                const float2 h = make_float2((float)v.x, (float)v.y);
+                sval32[16 * slot + 4 * p + r] = h;
+                sval32lo[16 * slot + 4 * p + r] =
+                    make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+            }
         }
 }
 
@@ -131,8 +137,13 @@ void assemble_matrix(ect_ctx* c, int which, int precision_mask) {
     M.sval.alloc(sizeof(double2) * 16 * nnzb);
     M.t.alloc(sizeof(double) * 4 * N);
     bool f32 = (precision_mask & ECT_F32) != 0;
-    if (f32) M.sval32.alloc(sizeof(float2) * 16 * nnzb);
-    else M.sval32.release();
+    if (f32) {
+        M.sval32.alloc(sizeof(float2) * 16 * nnzb);
+        M.sval32lo.alloc(sizeof(float2) * 16 * nnzb);
+    } else {
+        M.sval32.release();
+        M.sval32lo.release();
+    }
     k_assemble<<<grid_for(nnzb, 128), 128, 0, st>>>(
         c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), c->slot_ptr.as<int32_t>(), c->entries.as<uint32_t>(),
         c->geo.as<double>(), M.sigma.as<double>(), M.nu.as<double>(), M.fixmask.as<uint8_t>(), N, nnzb,
@@ -143,7 +154,8 @@ void assemble_matrix(ect_ctx* c, int which, int precision_mask) {
     ECT_CHECK_LAUNCH();
     k_scale_matrix<<<grid_for(nnzb, 128), 128, 0, st>>>(M.val.as<double2>(), c->row_ptr.as<int32_t>(),
                                                         c->col.as<int32_t>(), M.t.as<double>(), N, nnzb,
-                                                        M.sval.as<double2>(), f32 ? M.sval32.as<float2>() : nullptr);
+                                                        M.sval.as<double2>(), f32 ? M.sval32.as<float2>() : nullptr,
+                                                        f32 ? M.sval32lo.as<float2>() : nullptr);
     ECT_CHECK_LAUNCH();
     M.assembled = true;
     M.has_f32 = f32;

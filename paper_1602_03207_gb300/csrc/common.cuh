@@ -187,6 +187,7 @@ struct Matrix {
     DevBuf val;            // double2[nnzb*16] unscaled, constrained
     DevBuf sval;           // double2[nnzb*16] scaled  S = T M T
     DevBuf sval32;         // float2 [nnzb*16] scaled
+    DevBuf sval32lo;       // float2 [nnzb*16] FP32 remainder: sval ~= sval32 + sval32lo to ~2^-48
     DevBuf t;              // double[4N] scaling
     DevBuf pinv;           // double2 block inverses (column-major per block)
     DevBuf pinv32;         // float2  block inverses
@@ -213,7 +214,7 @@ struct Matrix {
         coarse_group = 0;
         coarse_k = 0;
         h_cond.clear();
-        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
+        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &sval32lo, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
                           &agg_lo, &agg_hi, &zv, &zv32, &rc, &zc, &gpart})
             b->release();
     }
@@ -291,6 +292,10 @@ void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, 
               int rhs_tile, const int* active);
 void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t ldx, int rhs_tile,
               const int* active);
+// y (FP64) = S u for u exactly representable in FP32 (double-float arithmetic
+// on sval32 + sval32lo); used by the mixed mode's outer Arnoldi step
+void spmv_df32(ect_ctx* c, int which, const float2* u, double2* y, int k, int64_t ldx, int rhs_tile,
+               const int* active);
 void precond_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld,
                        int rhs_tile, const int* active);
 void precond_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld,

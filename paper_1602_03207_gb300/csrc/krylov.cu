@@ -15,7 +15,7 @@
 // built from a multi-vector dot (per-CTA partial sums with warp shuffles,
 // then a fixed-order reduction, so results are bitwise reproducible), a
 // kernel that applies the first update and forms the second pass's dots and
-// ||w||^2 in the same pass over the basis (up to 16 vectors in FP32, 8 in
+// ||w||^2 in the same pass over the basis (up to 12 vectors in FP32, 8 in
 // FP64; two separate passes beyond), a multi-vector axpy that also
 // accumulates ||w||^2, and a
 // per-right-hand-side finalize kernel that applies the previous Givens
@@ -78,6 +78,26 @@ __device__ __forceinline__ void chunk_range(int64_t n, int G, int g, int64_t& lo
     if (hi > n) hi = n;
 }
 
+// One group of NQ basis vectors of the multi-dot.  The vector indices are
+// clamped to the last one, so every load is unconditional and the loads of a
+// step issue together (predicated loads would be serialised by branches); the
+// partial sums of the clamped duplicates are computed and never stored.
+template <typename T, int NQ>
+__device__ __forceinline__ void mdot_group(const C<T>* __restrict__ vr, int64_t vstride, int i0, int nvec,
+                                           const C<T>* __restrict__ w, int64_t lo, int64_t hi, C<T> (&acc)[GV],
+                                           T& wn) {
+    const C<T>* vq[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) vq[q] = vr + (int64_t)(i0 + q < nvec ? i0 + q : nvec - 1) * vstride;
+#pragma unroll 2  // independent elements: more loads in flight
+    for (int64_t e = lo + threadIdx.x; e < hi; e += TPB) {
+        const C<T> we = w[e];
+        wn += we.x * we.x + we.y * we.y;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) cfma_conj(acc[q], vq[q][e], we);
+    }
+}
+
 // part[(r*nvec + i)*G + g] = sum over this CTA's range of conj(V_i[r][e]) * W[r][e]
 // and, when wpart is given, wpart[r*G + g] = sum of |W[r][e]|^2 over the range
 template <typename T>
@@ -91,18 +111,14 @@ __global__ void __launch_bounds__(TPB) k_mdot(const C<T>* __restrict__ V, int64_
     int64_t lo, hi;
     chunk_range(n, G, g, lo, hi);
     const C<T>* w = W + (int64_t)r * ld;
+    const C<T>* vr = V + (int64_t)r * ld;
     for (int i0 = 0; i0 < nvec; i0 += GV) {
         C<T> acc[GV];
         T wn = T(0);
 #pragma unroll
         for (int q = 0; q < GV; ++q) acc[q] = czero<T>();
-        for (int64_t e = lo + threadIdx.x; e < hi; e += TPB) {
-            const C<T> we = w[e];
-            wn += we.x * we.x + we.y * we.y;
-#pragma unroll
-            for (int q = 0; q < GV; ++q)
-                if (i0 + q < nvec) cfma_conj(acc[q], V[(int64_t)(i0 + q) * vstride + (int64_t)r * ld + e], we);
-        }
+        if (nvec - i0 > GV / 2) mdot_group<T, GV>(vr, vstride, i0, nvec, w, lo, hi, acc, wn);
+        else mdot_group<T, GV / 2>(vr, vstride, i0, nvec, w, lo, hi, acc, wn);
         double s[2 * GV + 1];
 #pragma unroll
         for (int q = 0; q < GV; ++q) {
@@ -136,9 +152,9 @@ __global__ void __launch_bounds__(TPB, 2) k_maxpy_mdot(const C<T>* __restrict__ 
     __shared__ double sh[8 * (2 * GV + 1)];
     const int r = blockIdx.y, g = blockIdx.x;
     if (live && !live[r]) return;
-    for (int i = threadIdx.x; i < nvec; i += TPB) {
-        const double2 h = hp[(int64_t)r * ldp + i];
-        hs[i] = from_d<T>(make_double2(-h.x, -h.y));
+    for (int i = threadIdx.x; i < NV; i += TPB) {
+        const double2 h = i < nvec ? hp[(int64_t)r * ldp + i] : make_double2(0.0, 0.0);
+        hs[i] = from_d<T>(make_double2(-h.x, -h.y));  // zero beyond nvec: the padded terms add nothing
     }
     __syncthreads();
     int64_t lo, hi;
@@ -149,20 +165,21 @@ __global__ void __launch_bounds__(TPB, 2) k_maxpy_mdot(const C<T>* __restrict__ 
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = czero<T>();
     T nacc = T(0);
+    // vector indices clamped to the last one: unconditional loads (see mdot_group)
+    const C<T>* vq[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) vq[q] = vr + (int64_t)(q < nvec ? q : nvec - 1) * vstride;
     for (int64_t e = lo + threadIdx.x; e < hi; e += TPB) {
         C<T> v[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (q < nvec) v[q] = vr[(int64_t)q * vstride + e];
+        for (int q = 0; q < NV; ++q) v[q] = vq[q][e];
         C<T> we = w[e];
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (q < nvec) cfma(we, hs[q], v[q]);
+        for (int q = 0; q < NV; ++q) cfma(we, hs[q], v[q]);
         w[e] = we;
         nacc += we.x * we.x + we.y * we.y;
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (q < nvec) cfma_conj(acc[q], v[q], we);
+        for (int q = 0; q < NV; ++q) cfma_conj(acc[q], v[q], we);
     }
     // reduce in groups of GV vectors (bounded register use); the norm rides with the first group
 #pragma unroll
@@ -171,8 +188,9 @@ __global__ void __launch_bounds__(TPB, 2) k_maxpy_mdot(const C<T>* __restrict__ 
         double s[2 * GV + 1];
 #pragma unroll
         for (int q = 0; q < GV; ++q) {
-            s[2 * q] = (double)acc[i0 + q].x;
-            s[2 * q + 1] = (double)acc[i0 + q].y;
+            const int iq = i0 + q < NV ? i0 + q : 0;  // NV need not be a multiple of GV
+            s[2 * q] = i0 + q < NV ? (double)acc[iq].x : 0.0;
+            s[2 * q + 1] = i0 + q < NV ? (double)acc[iq].y : 0.0;
         }
         s[2 * GV] = (double)nacc;
         block_sum<2 * GV + 1>(s, sh);
@@ -251,6 +269,7 @@ __global__ void __launch_bounds__(TPB) k_maxpy(const C<T>* __restrict__ V, int64
     chunk_range(n, G, g, lo, hi);
     C<T>* w = W + (int64_t)r * ld;
     T nacc = T(0);
+#pragma unroll 2
     for (int64_t e = lo + threadIdx.x; e < hi; e += TPB) {
         C<T> we = w[e];
         for (int i = 0; i < nvec; ++i) cfma(we, hs[i], V[(int64_t)i * vstride + (int64_t)r * ld + e]);
@@ -275,6 +294,7 @@ __global__ void __launch_bounds__(TPB) k_norm_part(const C<T>* __restrict__ W, i
     chunk_range(n, G, g, lo, hi);
     const C<T>* w = W + (int64_t)r * ld;
     T nacc = T(0);
+#pragma unroll 4
     for (int64_t e = lo + threadIdx.x; e < hi; e += TPB) {
         C<T> we = w[e];
         nacc += we.x * we.x + we.y * we.y;
@@ -596,13 +616,16 @@ void cgs2_step(ect_ctx* c, Workspace* w, const C<T>* V, int64_t vstride, int j, 
     k_mdot<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live, part, G, sel ? w->wpart.as<double>() : nullptr);
     k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live, hp, ldp, H, ldh, hoff, 0);
     // w1 = w - V h1, fused with h2 = V^H w1 and ||w1||^2 when the basis fits the register tile
-    // (16 vectors in FP32, 8 in FP64: beyond that the registers cut occupancy below the two-pass cost)
+    // (12 vectors in FP32, 8 in FP64: beyond that the registers spill or cut occupancy below the
+    // two-pass cost)
     bool fused = true;
-    if (nvec <= 8)
+    constexpr bool f32 = std::is_same<T, float>::value;
+    if (nvec <= 4)
+        k_maxpy_mdot<T, 4><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
+    else if (nvec <= 8)
         k_maxpy_mdot<T, 8><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
-    else if (std::is_same<T, float>::value && nvec <= 16)
-        k_maxpy_mdot<T, std::is_same<T, float>::value ? 16 : 8>
-            <<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
+    else if (f32 && nvec <= 12)
+        k_maxpy_mdot<T, f32 ? 12 : 8><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, live, part, npart, G);
     else {
         fused = false;
         k_maxpy<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live, sel ? npart : nullptr, G);
@@ -674,9 +697,15 @@ void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
         double2* Vj = V + (int64_t)j * vs;
         double2* Vn = V + (int64_t)(j + 1) * vs;
         double2* Zj = Z + (int64_t)j * vs;
-        if (w->mode == ECT_MODE_MIXED) inner_solve(c, w, which, Vj, Zj, rhs_tile);
-        else precond_apply_f64(c, which, Vj, Zj, k, ld, rhs_tile, live);
-        spmv_f64(c, which, true, Zj, Vn, k, ld, rhs_tile, live);
+        if (w->mode == ECT_MODE_MIXED) {
+            // Z_j is the FP32 inner solution (U32) widened: its product with S is formed in
+            // double-float arithmetic from the FP32 copy and remainder of S
+            inner_solve(c, w, which, Vj, Zj, rhs_tile);
+            spmv_df32(c, which, w->U32.as<float2>(), Vn, k, ld, rhs_tile, live);
+        } else {
+            precond_apply_f64(c, which, Vj, Zj, k, ld, rhs_tile, live);
+            spmv_f64(c, which, true, Zj, Vn, k, ld, rhs_tile, live);
+        }
         cgs2_step<double>(c, w, V, vs, j, Vn, ld, w->H.as<double2>(), m, live);
         k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
             w->npart.as<double>(), w->G, k, j, m, w->H.as<double2>(), w->cs.as<double>(), w->sn.as<double2>(),

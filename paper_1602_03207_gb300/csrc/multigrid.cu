@@ -30,6 +30,7 @@
 namespace {
 
 constexpr int AGG_SIZE = 8;
+constexpr int64_t WARP_ROW_MAX_NODES = 16384;  // levels up to this size use the warp-per-row SpMM
 constexpr int64_t MAX_COARSE_DOFS = 2048;
 
 // coarse block values: sum over the fine blocks mapped to each coarse block of
@@ -228,7 +229,7 @@ struct MgLevel {
     const float2* d_pinv32 = nullptr;
     DevBuf agg_ptr_own, pinv_off_own, pinv32_off_own, pinv64_own, pinv32_own;
     DevBuf node_agg, clo, chi, w64, w32;
-    DevBuf ap_ptr, ap_col, ap_val64, ap_val32;  // AP (finest level only)
+    DevBuf ap_ptr, ap_col, ap_val64, ap_val32;  // AP = A P (this level's rows, next level's columns)
     bool has_ap = false;
     DevBuf r, z, t;                          // cycle vectors (k right-hand sides)
 };
@@ -525,7 +526,7 @@ void mg_setup(ect_ctx* c, int which, bool f32) {
         to_device(L.clo, lo, st);
         to_device(L.chi, hi, st);
         L.n_next = na;
-        if (depth == 0) build_ap(st, L, nagg, f32);
+        build_ap(st, L, nagg, f32);
         ECT_CUDA(cudaStreamSynchronize(st));
         if (coarsest) {
             const int64_t nc = 4 * na;
@@ -620,9 +621,10 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
     const T* w = lvl_w<T>(L);
     block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, r, z, k, ld, tile, active, false);
     const int gamma = last ? 1 : 2;
-    // t = r - A z: one thread per scalar row on the finest level, one warp per block row below
+    // t = r - A z: one thread per scalar row, or one warp per block row on the small coarse
+    // levels (few rows, many blocks per row: the warp splits the row's serial chain of loads)
     auto residual = [&]() {
-        if (l > 0)
+        if (L.n <= WARP_ROW_MAX_NODES)
             bsr_spmv_warp<T>(st, L.rp, L.col, val, L.n, z, r, t, k, ld, tile, active);
         else if (std::is_same<T, double>::value)
             bsr_spmv_f64(st, L.rp, L.col, (const double2*)val, L.n, (const double2*)z, (const double2*)r, (double2*)t,

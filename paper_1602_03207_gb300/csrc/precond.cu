@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(64) k_block_apply_sym(const int32_t* __restric
                                                         const float2* __restrict__ zc, int64_t nc,
                                                         const float* __restrict__ zv, int accumulate, int ntile) {
     __shared__ float4 S4[SYM_MAX_F4];
-    __shared__ float2 rs[KT][64];
+    __shared__ __align__(16) float2 rs[64][KT];  // [row][rhs]: one step reads its KT values as float4s
     const int blk = (int)(blockIdx.x / ntile), tid = threadIdx.x;
     const int r0 = (int)(blockIdx.x % ntile) * KT;
     const int n0 = block_ptr[blk], n1 = block_ptr[blk + 1];
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(64) k_block_apply_sym(const int32_t* __restric
     for (int e = tid; e < n4; e += 64) S4[e] = __ldg(P4 + e);
 #pragma unroll
     for (int q = 0; q < KT; ++q)
-        if (on[q] && tid < b) rs[q][tid] = r[(int64_t)(r0 + q) * ld + base + tid];
+        if (on[q] && tid < b) rs[tid][q] = r[(int64_t)(r0 + q) * ld + base + tid];
     __syncthreads();
     if (tid >= b) return;
     const float2* S = reinterpret_cast<const float2*>(S4);
@@ -232,8 +232,17 @@ __global__ void __launch_bounds__(64) k_block_apply_sym(const int32_t* __restric
 #pragma unroll 4
     for (int j = 0; j < b; ++j) {
         const float2 a = S[j >= tid ? tj + tid : ti + j];
+        if constexpr (KT >= 2) {
+            const float4* rj = reinterpret_cast<const float4*>(rs[j]);
 #pragma unroll
-        for (int q = 0; q < KT; ++q) cfma(acc[q], a, rs[q][j]);
+            for (int h = 0; h < KT / 2; ++h) {
+                const float4 v = rj[h];
+                cfma(acc[2 * h], a, make_float2(v.x, v.y));
+                cfma(acc[2 * h + 1], a, make_float2(v.z, v.w));
+            }
+        } else {
+            cfma(acc[0], a, rs[j][0]);
+        }
         tj += j + 1;
     }
     if (zc && (tid & 3) == 3) {

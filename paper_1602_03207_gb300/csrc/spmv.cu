@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_spmv_f64(const int32_t* __restrict__ ro
 }
 
 template <int KT>
-__global__ void __launch_bounds__(256) k_spmv_f32(const int32_t* __restrict__ row_ptr,
+__global__ void __launch_bounds__(256, 4) k_spmv_f32(const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col,
                                                   const float2* __restrict__ val, const float2* __restrict__ x,
                                                   float2* __restrict__ y, int64_t n_rows, int64_t ld,
@@ -220,6 +220,78 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const int32_t* __restrict__ r
         }
 }
 
+// Double-float accumulation of one real product (a_hi + a_lo) u into (S, c):
+// p = a_hi u rounded, e its exact rounding error plus a_lo u, then Knuth's
+// TwoSum adds p to S exactly (the error goes to c).  Round-to-nearest
+// intrinsics keep the compiler from fusing the steps.
+__device__ __forceinline__ void df32_acc(float& S, float& c, float ah, float al, float u) {
+    const float p = __fmul_rn(ah, u);
+    float e = __fmaf_rn(ah, u, -p);
+    e = __fmaf_rn(al, u, e);
+    const float t = __fadd_rn(S, p);
+    const float bp = __fsub_rn(t, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    S = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// Outer-loop SpMM of the mixed mode: y (FP64) = S u where u is exactly
+// representable in FP32 (the inner FP32 solution).  S = S_hi + S_lo, both in
+// FP32; every product is formed exactly up to the dropped ~2^-48 terms and
+// summed in double-float, so y matches the FP64 product to about 2^-46 of
+// sum |S_ij u_j| while the arithmetic runs on the FP32 pipe (GB300's FP64
+// rate makes the plain FP64 product ALU-bound at several times the time).
+template <int KT>
+__global__ void __launch_bounds__(256) k_spmv_df32(const int32_t* __restrict__ row_ptr,
+                                                   const int32_t* __restrict__ col,
+                                                   const float2* __restrict__ vhi, const float2* __restrict__ vlo,
+                                                   const float2* __restrict__ x, double2* __restrict__ y,
+                                                   int64_t n_rows, int64_t ld, const int* __restrict__ active,
+                                                   int ntile) {
+    const int tile = (int)(blockIdx.x % ntile);
+    const int64_t d = (int64_t)(blockIdx.x / ntile) * blockDim.x + threadIdx.x;
+    if (d >= 4 * n_rows) return;
+    const int row = (int)(d >> 2), p = (int)(d & 3);
+    const int r0 = tile * KT;
+    bool on[KT], any = false;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+        on[q] = !active || active[r0 + q];
+        any |= on[q];
+    }
+    if (!any) return;
+    float sr[KT], cr[KT], si[KT], ci[KT];
+#pragma unroll
+    for (int q = 0; q < KT; ++q) sr[q] = cr[q] = si[q] = ci[q] = 0.f;
+    const int s1 = row_ptr[row + 1];
+    for (int s = row_ptr[row]; s < s1; ++s) {
+        const int c = col[s];
+        const float4* vh = reinterpret_cast<const float4*>(vhi + 16 * (int64_t)s + 4 * p);
+        const float4* vl = reinterpret_cast<const float4*>(vlo + 16 * (int64_t)s + 4 * p);
+        const float4 h01 = vh[0], h23 = vh[1], l01 = vl[0], l23 = vl[1];
+        const float ahr[4] = {h01.x, h01.z, h23.x, h23.z}, ahi[4] = {h01.y, h01.w, h23.y, h23.w};
+        const float alr[4] = {l01.x, l01.z, l23.x, l23.z}, ali[4] = {l01.y, l01.w, l23.y, l23.w};
+#pragma unroll
+        for (int q = 0; q < KT; ++q) {
+            const float4* xv = reinterpret_cast<const float4*>(x + (int64_t)(r0 + q) * ld + 4 * (int64_t)c);
+            const float4 x01 = xv[0], x23 = xv[1];
+            const float ur[4] = {x01.x, x01.z, x23.x, x23.z}, ui[4] = {x01.y, x01.w, x23.y, x23.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                df32_acc(sr[q], cr[q], ahr[e], alr[e], ur[e]);
+                df32_acc(sr[q], cr[q], -ahi[e], -ali[e], ui[e]);
+                df32_acc(si[q], ci[q], ahr[e], alr[e], ui[e]);
+                df32_acc(si[q], ci[q], ahi[e], ali[e], ur[e]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if (on[q])
+            y[(int64_t)(r0 + q) * ld + d] =
+                make_double2((double)sr[q] + (double)cr[q], (double)si[q] + (double)ci[q]);
+}
+
 }  // namespace
 
 void bsr_spmv_f64(cudaStream_t st, const int32_t* rp, const int32_t* cl, const double2* val, int64_t N,
@@ -314,3 +386,27 @@ template void bsr_spmv_warp<double>(cudaStream_t, const int32_t*, const int32_t*
                                     const double2*, const double2*, double2*, int, int64_t, int, const int*);
 template void bsr_spmv_warp<float>(cudaStream_t, const int32_t*, const int32_t*, const float2*, int64_t, const float2*,
                                    const float2*, float2*, int, int64_t, int, const int*);
+
+void spmv_df32(ect_ctx* c, int which, const float2* u, double2* y, int k, int64_t ldx, int rhs_tile,
+               const int* active) {
+    Matrix& M = c->mat[which];
+    ECT_REQUIRE(M.assembled && M.has_f32, ECT_ERR_STATE, "FP32 matrix not assembled (use ECT_F32 in ect_assemble)");
+    const int32_t* rp = c->row_ptr.as<int32_t>();
+    const int32_t* cl = c->col.as<int32_t>();
+    const float2* hi = M.sval32.as<float2>();
+    const float2* lo = M.sval32lo.as<float2>();
+    const int64_t N = c->n_nodes;
+    for_tiles(k, rhs_tile, [&](int kt, int r, int nt) {
+        const unsigned grid = tile_grid(grid_for(4 * N, 256), nt);
+        const float2* xr = u + r * ldx;
+        double2* yr = y + r * ldx;
+        const int* ar = active ? active + r : nullptr;
+        switch (kt) {
+            case 8: k_spmv_df32<8><<<grid, 256, 0, c->stream>>>(rp, cl, hi, lo, xr, yr, N, ldx, ar, nt); break;
+            case 4: k_spmv_df32<4><<<grid, 256, 0, c->stream>>>(rp, cl, hi, lo, xr, yr, N, ldx, ar, nt); break;
+            case 2: k_spmv_df32<2><<<grid, 256, 0, c->stream>>>(rp, cl, hi, lo, xr, yr, N, ldx, ar, nt); break;
+            default: k_spmv_df32<1><<<grid, 256, 0, c->stream>>>(rp, cl, hi, lo, xr, yr, N, ldx, ar, nt); break;
+        }
+    });
+    ECT_CHECK_LAUNCH();
+}

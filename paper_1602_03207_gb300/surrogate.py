@@ -87,7 +87,9 @@ class DatasetGenerator:
         self.ctx.set_defect(sd, nd)
         self.ctx.assemble(E.ECT_DEFECT, mask)
         self.ctx.precond_setup(E.ECT_DEFECT, mask, -1)
+        t1 = time.perf_counter()
         st = self.ctx.solve(E.ECT_DEFECT, self.B, self.Ud, self.z.size, self.opts)
+        t2 = time.perf_counter()
         dz = np.empty(self.z.size, dtype=np.complex128)
         I = [self.current, self.current]
         for q in range(self.z.size):
@@ -95,8 +97,10 @@ class DatasetGenerator:
             ud = self.Ud[q].unsqueeze(0).expand(2, -1).contiguous()
             d, _ = self.ctx.delta_z(u0, ud, None, I)
             dz[q] = d[0, 0]
+        t3 = time.perf_counter()
         return {"seed": int(seed), "params": [float(v) for v in params], "dz_re": dz.real.tolist(),
-                "dz_im": dz.imag.tolist(), "iters": st["iters"], "seconds": time.perf_counter() - t0}
+                "dz_im": dz.imag.tolist(), "iters": st["iters"], "seconds": t3 - t0,
+                "seconds_setup": t1 - t0, "seconds_solve": t2 - t1, "seconds_dz": t3 - t2}
 
     def run(self, seeds, path, budget_s=None):
         done = load_samples(path)

@@ -218,9 +218,14 @@ __global__ void __launch_bounds__(64) k_block_apply_sym(const int32_t* __restric
     if (!any) return;  // the whole tile has retired (uniform over the CTA, before any barrier)
     const float4* P4 = reinterpret_cast<const float4*>(pinv + poff[blk]);
     for (int e = tid; e < n4; e += 64) S4[e] = __ldg(P4 + e);
+    unsigned onm = 0;
 #pragma unroll
-    for (int q = 0; q < KT; ++q)
-        if (on[q] && tid < b) rs[tid][q] = r[(int64_t)(r0 + q) * ld + base + tid];
+    for (int q = 0; q < KT; ++q) onm |= on[q] ? 1u << q : 0u;
+    // flat mapping: consecutive threads fill consecutive shared words (no bank conflicts)
+    for (int f = tid; f < 64 * KT; f += 64) {
+        const int row = f / KT, q = f - row * KT;
+        if (row < b && ((onm >> q) & 1u)) rs[row][q] = r[(int64_t)(r0 + q) * ld + base + row];
+    }
     __syncthreads();
     if (tid >= b) return;
     const float2* S = reinterpret_cast<const float2*>(S4);

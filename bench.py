@@ -195,7 +195,7 @@ def run_gpu(args):
         t_at = time.time()
         mixed, tst = ctx.autotune(0, Bsrc, U0, k, base)
         tune = {"rhs_tile": mixed.rhs_tile, "restart": mixed.restart, "inner_iters": mixed.inner_iters,
-                "seconds": time.time() - t_at, "winner_ms": tst["ms"]}
+                "reorth": mixed.reorth, "seconds": time.time() - t_at, "winner_ms": tst["ms"]}
 
     stats = {}
 
@@ -306,7 +306,8 @@ def run_gpu(args):
         "config": {"workload": f"{args.config}: {m.n_nodes} nodes / {n} complex dof / {m.n_tets} tets, "
                                f"{P} probe positions per rank per step (= {4 * P} solves), tol {args.tol}",
                    "positions_per_step": P * world, "rhs_per_solve_call": k, "nnzb": nnzb,
-                   "inner_iters": args.inner_iters, "outer_restart": args.outer_restart,
+                   "inner_iters": mixed.inner_iters, "outer_restart": mixed.restart,
+                   "reorth": mixed.reorth, "rhs_tile": mixed.rhs_tile,
                    "l2": "inputs larger than L2 (matrices 3.8 GB FP64 / 1.9 GB FP32 each)",
                    "parallelism": f"positions sharded over {world} GPU(s)"},
         "clocks": clocks,

@@ -74,7 +74,9 @@ typedef struct {
                            -1 = FP32 SpMM variant that splits the tile over thread groups */
     double timeout_s;   /* wall-clock limit of one solve call (0 = none)                  */
     int reorth;         /* 0: always two Gram-Schmidt passes; 1: second pass only when the
-                           first removed more than half of ||w||^2 (default)             */
+                           first removed more than half of ||w||^2 (default); 2: as 1 in
+                           the FP64 loop, one classical pass in the mixed mode's FP32 loop;
+                           3: one classical pass in both loops                           */
 } ect_options;
 
 typedef struct {
@@ -202,8 +204,9 @@ int ect_solve(ect_ctx* ctx, int which, const void* d_rhs, void* d_x, int k,
  * (complex128 [k][n_nodes][4]): times the SpMM and preconditioner right-hand-
  * side tile (1, 2, 4, 8) with CUDA events, then runs full solves of d_rhs for
  * each (restart, inner_iters) candidate of the mode in *base and keeps the
- * fastest that converges.  *best receives *base with rhs_tile, restart and
- * inner_iters replaced; stats of the winning solve go to *stats (may be NULL).
+ * fastest that converges; in mixed mode the winner is also tried with reorth
+ * = 2 and 3.  *best receives *base with rhs_tile, restart, inner_iters and reorth
+ * replaced; stats of the winning solve go to *stats (may be NULL).
  * d_work: complex128 [k][n_nodes][4] scratch for the solutions.  Costs one
  * full solve per candidate; call it once per workload. */
 int ect_autotune(ect_ctx* ctx, int which, const void* d_rhs, void* d_work, int k, const ect_options* base,

@@ -288,6 +288,26 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
             }
         }
         ECT_REQUIRE(any, ECT_ERR_NOT_CONVERGED, "no autotune candidate converged");
+        if (mixed) {
+            // the winner again with one Gram-Schmidt pass in the FP32 loop (2), then in both loops (3)
+            const ect_options w0 = win;
+            for (int ro : {2, 3}) {
+                if (w0.reorth == ro) continue;
+                ect_options t = w0;
+                t.reorth = ro;
+                ect_stats s{};
+                try {
+                    solve(c, which, (const double2*)d_rhs, (double2*)d_work, k, t, &s);
+                    if (s.ms < best_t) {
+                        best_t = s.ms;
+                        win = t;
+                        wst = s;
+                    }
+                } catch (const EctError& e) {
+                    if (e.code != ECT_ERR_NOT_CONVERGED && e.code != ECT_ERR_TIMEOUT) throw;
+                }
+            }
+        }
         *best = win;
         if (stats) *stats = wst;
     });

@@ -518,6 +518,8 @@ struct Workspace {
     DevBuf part, npart, wpart;
     DevBuf bnorm, rnorm, target, target_i, inv_h, invb, run, live, live_i, nit, nit_i, flags, live2;
     bool selective = true;
+    bool inner_one_pass = false;  // mixed mode: one classical Gram-Schmidt pass in the FP32 loop
+    bool outer_one_pass = false;  // one classical Gram-Schmidt pass in the FP64 loop
     std::map<std::tuple<int, int, int, int, int>, std::pair<cudaGraphExec_t, size_t>> graphs;  // exec, kernel nodes
     ~Workspace() {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
@@ -600,7 +602,7 @@ inline unsigned ew_blocks(int64_t n, int k) {
 // one CGS2 Arnoldi step on basis vectors V_0..V_j (storage T), new vector W
 template <typename T>
 void cgs2_step(ect_ctx* c, Workspace* w, const C<T>* V, int64_t vstride, int j, C<T>* W, int64_t ld,
-               double2* H, int m, const int* live) {
+               double2* H, int m, const int* live, bool one_pass = false) {
     cudaStream_t st = c->stream;
     const int nvec = j + 1, k = w->k, G = w->G;
     const int64_t n = w->n;
@@ -615,6 +617,12 @@ void cgs2_step(ect_ctx* c, Workspace* w, const C<T>* V, int64_t vstride, int j, 
     // pass 1: h1 = V^H w
     k_mdot<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, live, part, G, sel ? w->wpart.as<double>() : nullptr);
     k_dot_reduce<<<rb, 256, 0, st>>>(part, G, nvec, k, live, hp, ldp, H, ldh, hoff, 0);
+    if (one_pass) {
+        // classical Gram-Schmidt: w -= V h1 and ||w||^2, no second pass
+        k_maxpy<T><<<vg, TPB, 0, st>>>(V, vstride, nvec, W, ld, n, hp, ldp, 1.0, live, npart, G);
+        ECT_CHECK_LAUNCH();
+        return;
+    }
     // w1 = w - V h1, fused with h2 = V^H w1 and ||w1||^2 when the basis fits the register tile
     // (12 vectors in FP32, 8 in FP64: beyond that the registers spill or cut occupancy below the
     // two-pass cost)
@@ -661,7 +669,7 @@ void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2*
         float2* Zj = Z32 + (int64_t)j * vs;
         precond_apply_f32(c, which, Vj, Zj, k, ld, rhs_tile, live_i);
         spmv_f32(c, which, Zj, Vn, k, ld, rhs_tile, live_i);
-        cgs2_step<float>(c, w, V32, vs, j, Vn, ld, w->Hi.as<double2>(), mi, live_i);
+        cgs2_step<float>(c, w, V32, vs, j, Vn, ld, w->Hi.as<double2>(), mi, live_i, w->inner_one_pass);
         k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
             w->npart.as<double>(), w->G, k, j, mi, w->Hi.as<double2>(), w->csi.as<double>(), w->sni.as<double2>(),
             w->gi.as<double2>(), w->target_i.as<double>(), live_i, w->nit_i.as<int>(), w->inv_h.as<double>(),
@@ -706,7 +714,7 @@ void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
             precond_apply_f64(c, which, Vj, Zj, k, ld, rhs_tile, live);
             spmv_f64(c, which, true, Zj, Vn, k, ld, rhs_tile, live);
         }
-        cgs2_step<double>(c, w, V, vs, j, Vn, ld, w->H.as<double2>(), m, live);
+        cgs2_step<double>(c, w, V, vs, j, Vn, ld, w->H.as<double2>(), m, live, w->outer_one_pass);
         k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
             w->npart.as<double>(), w->G, k, j, m, w->H.as<double2>(), w->cs.as<double>(), w->sn.as<double2>(),
             w->g.as<double2>(), w->target.as<double>(), live, w->nit.as<int>(), w->inv_h.as<double>(),
@@ -744,10 +752,13 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
     ECT_CUDA(cudaEventRecord(c->ev0, st));
     coarse_scratch(c, which, k);
     Workspace* w = get_ws(c, k, opt.restart, mi, opt.mode);
-    if (w->selective != (opt.reorth != 0)) {
+    const bool in1 = opt.reorth >= 2, out1 = opt.reorth == 3;
+    if (w->selective != (opt.reorth != 0) || w->inner_one_pass != in1 || w->outer_one_pass != out1) {
         for (auto& kv : w->graphs) cudaGraphExecDestroy(kv.second.first);
         w->graphs.clear();
         w->selective = opt.reorth != 0;
+        w->inner_one_pass = in1;
+        w->outer_one_pass = out1;
     }
     const int64_t n = w->n, ld = n;
     const double* t = M.t.as<double>();

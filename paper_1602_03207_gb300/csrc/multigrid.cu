@@ -526,7 +526,7 @@ void mg_setup(ect_ctx* c, int which, bool f32) {
         to_device(L.clo, lo, st);
         to_device(L.chi, hi, st);
         L.n_next = na;
-        build_ap(st, L, nagg, f32);
+        if (L.n > WARP_ROW_MAX_NODES) build_ap(st, L, nagg, f32);  // small levels: latency-bound either way
         ECT_CUDA(cudaStreamSynchronize(st));
         if (coarsest) {
             const int64_t nc = 4 * na;

@@ -147,8 +147,9 @@ def test_multigrid_apply_matches_oracle(ect, prec, shape):
 
     The cycle's output is dominated by the coarsest-level correction of the
     near-null (gauge) modes, eigenvalues ~1e-6 of the scaled operator, so
-    rounding differences are amplified by ~1e6: FP64 agrees to ~1e-8, FP32 to
-    ~3e-3.  The solve tests gate the final accuracy on the true residual."""
+    rounding differences are amplified by ~1e6: FP64 agrees to ~1e-8, FP32
+    (eps 6e-8) to 1e-3..1e-2 depending on the summation order of each level's
+    kernels.  The solve tests gate the final accuracy on the true residual."""
     p = E.wall_loss_problem(shape, (20e-3, 20e-3, 30e-3), (2, 2, 2), 0.15, 4, z_pos=(0.0,))
     ctx = make_ctx(ect, p, group=-1)
     M = fem.system_matrix(p, "defect")
@@ -158,14 +159,14 @@ def test_multigrid_apply_matches_oracle(ect, prec, shape):
     n = 4 * p.mesh.n_nodes
     k = 19                                       # two full tiles of 8, then 2 and 1
     R = crand(rng, k, n)
-    dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-7) if prec == "f64" else (torch.complex64, ect.ECT_F32, 1e-2))
+    dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-7) if prec == "f64" else (torch.complex64, ect.ECT_F32, 3e-2))
     r = dev(R, dt)
     z = torch.empty_like(r)
     ctx.precond_apply(1, r, z, k, precision=pr)
     Z = z.cpu().numpy()
-    for q in range(k):
-        ref = solve.amg_apply(lv, R[q])
-        assert np.linalg.norm(Z[q] - ref) <= tol * np.linalg.norm(ref), q
+    refs = [solve.amg_apply(lv, R[q]) for q in range(k)]
+    errs = [np.linalg.norm(Z[q] - refs[q]) / np.linalg.norm(refs[q]) for q in range(k)]
+    assert max(errs) <= tol, (int(np.argmax(errs)), max(errs), float(np.median(errs)))
 
 
 @pytest.mark.parametrize("mode", ["f64", "mixed"])
@@ -260,6 +261,16 @@ def test_solve_residual_with_oracle_matrix(ect, small, mode, graph):
     p, ctx, M = small
     opts = ect.default_options(tol=1e-10, restart=30, use_graph=graph,
                                mode=ect.ECT_MODE_F64 if mode == "f64" else ect.ECT_MODE_MIXED, inner_iters=20)
+    for w in WHICH:
+        X, st = _solve_check(ect, p, ctx, M, w, opts)
+        assert st["converged"] == 2
+
+
+@pytest.mark.parametrize("reorth", [0, 2, 3])
+def test_mixed_solve_gram_schmidt_variants(ect, small, reorth):
+    """Mixed mode with two passes always (0), one inner pass (2), one pass in both loops (3)."""
+    p, ctx, M = small
+    opts = ect.default_options(tol=1e-10, restart=16, mode=ect.ECT_MODE_MIXED, inner_iters=16, reorth=reorth)
     for w in WHICH:
         X, st = _solve_check(ect, p, ctx, M, w, opts)
         assert st["converged"] == 2

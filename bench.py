@@ -176,7 +176,8 @@ def run_gpu(args):
     zs = probe_positions(P, rank, world)
     cur = [c.current for c in p.coils]
     base = ect.default_options(tol=args.tol, mode=ect.ECT_MODE_MIXED, restart=args.outer_restart,
-                               inner_iters=args.inner_iters, max_iters=args.max_outer, use_graph=1)
+                               inner_iters=args.inner_iters, max_iters=args.max_outer, use_graph=1,
+                               reorth=args.reorth)
     plain = ect.default_options(tol=args.tol, mode=ect.ECT_MODE_F64, restart=args.restart, use_graph=1,
                                 max_iters=args.max_iters)
     # device-resident sources: [P][2][n] (position-major, coil minor)
@@ -464,6 +465,7 @@ def main():
     ap.add_argument("--outer-restart", type=int, default=10)
     ap.add_argument("--max-outer", type=int, default=400)
     ap.add_argument("--inner-iters", type=int, default=20)
+    ap.add_argument("--reorth", type=int, default=1, help="Gram-Schmidt variant when not autotuned (0-3)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel-probe", action="store_true", help="only launch the hot kernels on a mid-size case")
     ap.add_argument("--probe-mg", action="store_true")

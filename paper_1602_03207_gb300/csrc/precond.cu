@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(256) k_gemv_split(const C<T>* __restrict__ ein
     C<T> acc[KT];
 #pragma unroll
     for (int q = 0; q < KT; ++q) acc[q] = czero<T>();
+#pragma unroll 8  // independent loads of the chunk's columns in flight together
     for (int d = 0; d < dn; ++d) {
         const C<T> a = einv[(d0 + d) * nc + cc];
 #pragma unroll

@@ -124,6 +124,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, device):
+    """Max of a host scalar over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the max-over-ranks time."""
+    return units_per_rank * world / seconds
+
+
 def probe_positions(n, rank=0, world=1):
     """Positions around the plate edge (z = 10 mm), 0.5 mm apart, sharded by rank."""
     z = 10.0e-3 + 0.5e-3 * (np.arange(n * world) - (n * world) // 2)
@@ -226,11 +242,8 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     if world > 1:
         dist.barrier()
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    solves = 4 * P * world * args.steps
-    value = solves / (ms / 1000.0)
+    ms = max_over_ranks(ms, "cuda")
+    value = job_rate(4 * P * args.steps, world, ms / 1000.0)
 
     # e2e: the public host-buffer call (host positions in, host Delta Z out)
     torch.cuda.synchronize()
@@ -239,12 +252,8 @@ def run_gpu(args):
     for _ in range(args.steps):
         dz_e2e, _ = ctx.impedance(p.coils, zs, mixed)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t1
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = 4 * P * world * args.steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t1, "cuda")
+    e2e = job_rate(4 * P * args.steps, world, e2e_s)
 
     # plain FP64 flexible GMRES, one position (4 solves), the same preconditioner in FP64
     plain_ms = None

@@ -209,10 +209,18 @@ def run_gpu(args):
     tune = None
     mixed = base
     if not args.no_autotune:
+        # tune on each of the step's two systems, then keep the winner whose vacuum + defect
+        # solves take least time (one option set serves both, as in ect_impedance)
         t_at = time.time()
-        mixed, tst = ctx.autotune(0, Bsrc, U0, k, base)
+        cands = [ctx.autotune(w, Bsrc, U0, k, base)[0] for w in (0, 1)]
+        best_ms = None
+        for o in cands:
+            ms_pair = ctx.solve(0, Bsrc, U0, k, o)["ms"] + ctx.solve(1, Bsrc, Ud, k, o)["ms"]
+            if best_ms is None or ms_pair < best_ms:
+                mixed, best_ms = o, ms_pair
         tune = {"rhs_tile": mixed.rhs_tile, "restart": mixed.restart, "inner_iters": mixed.inner_iters,
-                "reorth": mixed.reorth, "seconds": time.time() - t_at, "winner_ms": tst["ms"]}
+                "reorth": mixed.reorth, "seconds": time.time() - t_at, "pair_ms": best_ms,
+                "tuned_on": "vacuum and defect systems; the faster option set on both"}
 
     stats = {}
 

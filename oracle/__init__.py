@@ -15,7 +15,8 @@ Modules
   impedance  Delta Z by reciprocity and by coil EMF (Eq. impedkl, impedmod)
   mlp        FP64 reference MLP for the surrogate (forward, backward, Adam)
 
-Parity status: the element matrices, the assembly, the solves and Delta Z are
-pinned by closed forms, invariants and brute force (see tests/).  Against the
-paper itself parity is unpinned: the paper prints no field or impedance value.
+Pins: every function is pinned by closed forms, invariants, special cases
+that reduce to a textbook routine and brute force on tiny inputs (see tests/,
+the test_oracle_* files).  The paper prints no field or impedance value, so
+no pin is a number copied from it.
 """

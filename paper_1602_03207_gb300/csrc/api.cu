@@ -263,7 +263,7 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
         o.rhs_tile = best_tile;
         // 2. Krylov lengths: full solves, fastest converged wins
         std::vector<std::pair<int, int>> cand;
-        if (mixed) cand = {{10, 10}, {10, 20}, {8, 30}, {16, 12}, {16, 16}, {12, 24}, {16, 20}};
+        if (mixed) cand = {{10, 10}, {10, 20}, {8, 30}, {16, 12}, {16, 16}, {12, 24}, {16, 20}, {16, 24}};
         else cand = {{20, 0}, {30, 0}, {45, 0}};
         double best_t = 1e300;
         ect_options win = o;

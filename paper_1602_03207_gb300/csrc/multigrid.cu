@@ -15,7 +15,10 @@
 // neighbours in increasing order, at most 8 nodes) and renumbered so that
 // aggregates are contiguous; the coarsest level (<= 2048 unknowns) is
 // inverted densely.  The cycle is a W-cycle with one block-Jacobi sweep
-// before and after the coarse corrections.
+// before and after the coarse corrections.  On the levels above 16k nodes the
+// residual after each coarse correction z += P e is updated as t -= (AP) e
+// instead of recomputed (AP = A P, built next to the Galerkin product); the
+// small levels recompute it with the warp-per-row SpMM.
 //
 // Setup runs once per matrix: patterns and aggregation on the host (integer
 // work), Galerkin values on the device (one thread per coarse block sums its

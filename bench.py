@@ -428,7 +428,8 @@ def run_reference(args):
     value = statistics.median([x["value"] for x in v])
     rec = {"impl": "reference", "metric": "probe solves/s at 4M complex DOF, FP64 plain vs mixed+batched, "
            "dZ err<=1e-6", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": 4 * args.positions * 1000.0 / value,
+           "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded, ect_inputs)",
            "config": {"workload": f"{args.config} (oracle sample)"},
            "cpu_baseline": dict(v[-1], value=value),

@@ -472,6 +472,49 @@ def kernel_probe(args):
                       "preconditioner": "multigrid" if args.probe_mg else "block-Jacobi"}))
 
 
+def mlp_probe(args):
+    """Surrogate MLP on the tensor cores: forward and one Adam step at batch 65536 (the largest the
+    library takes), timed with CUDA events; FLOPs count the real layer sizes (6->256, 4x 256->256)."""
+    import torch
+
+    from paper_1602_03207_gb300 import build as B
+    from paper_1602_03207_gb300 import ect
+
+    B.build()
+    bt = 65536
+    net = ect.Surrogate(batch=bt)
+    rng = np.random.default_rng(0)
+    sizes = ect.MLP_SIZES
+    layers = [(rng.normal(scale=1.0 / np.sqrt(fi), size=(fo, fi)), np.zeros(fo)) for fi, fo in zip(sizes[:-1], sizes[1:])]
+    net.set_params(ect.mlp_flatten(layers))
+    x = torch.randn(bt, sizes[0], device="cuda")
+    y = torch.empty(bt, sizes[-1], device="cuda")
+    t = torch.randn(bt, sizes[-1], device="cuda") * 0.1
+    fwd_flop = 2.0 * bt * sum(fi * fo for fi, fo in zip(sizes[:-1], sizes[1:]))
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    f_ms = timed(lambda: net.forward(x, y), 20)
+    s_ms = timed(lambda: net.train_step(x, t, 1e-4), 10)
+    peaks, src = load_peaks()
+    pk = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+    rec = {"mlp_probe": "ok", "batch": bt, "forward_ms": f_ms, "forward_tflops": fwd_flop / f_ms / 1e9,
+           "train_step_ms": s_ms, "train_step_tflops": 3 * fwd_flop / s_ms / 1e9,
+           "bf16_peak_tflops": pk, "peak_source": src,
+           "forward_frac": fwd_flop / f_ms / 1e9 / pk, "train_step_frac": 3 * fwd_flop / s_ms / 1e9 / pk}
+    print(json.dumps(rec))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,6 +533,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel-probe", action="store_true", help="only launch the hot kernels on a mid-size case")
     ap.add_argument("--probe-mg", action="store_true")
+    ap.add_argument("--mlp-probe", action="store_true", help="only time the surrogate MLP on the tensor cores")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -498,6 +542,9 @@ def main():
     args = ap.parse_args()
     if args.kernel_probe:
         kernel_probe(args)
+        return
+    if args.mlp_probe:
+        mlp_probe(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -372,6 +372,27 @@ def test_bad_meshes_rejected(ect):
     assert e.value.code == ect.ECT_ERR_STATE
 
 
+def test_empty_and_oversized_batches_rejected(ect, small):
+    """k = 0 and k beyond the documented limits are argument errors, reported before any work."""
+    p, ctx, M = small
+    n = 4 * p.mesh.n_nodes
+    b = torch.zeros(1, n, dtype=torch.complex128, device="cuda")
+    x = torch.empty_like(b)
+    for k in (0, 4097):
+        with pytest.raises(ect.EctError) as e:
+            ctx.solve(0, b, x, k)
+        assert e.value.code == ect.ECT_ERR_ARG, k
+    with pytest.raises(ect.EctError) as e:
+        ctx.spmv(0, b, x, 0)
+    assert e.value.code == ect.ECT_ERR_ARG
+    with pytest.raises(ect.EctError) as e:
+        ctx.coil_rhs(p.coils[0], np.zeros(0), b)
+    assert e.value.code == ect.ECT_ERR_ARG
+    for batch in (0, 100, 65536 + 256):
+        with pytest.raises(ect.EctError):
+            ect.Surrogate(batch=batch)
+
+
 def test_autotune_returns_converging_options(ect, small):
     p, ctx, M = small
     n = 4 * p.mesh.n_nodes

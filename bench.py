@@ -33,6 +33,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -85,7 +86,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples beside the process (summarised into the JSON line); ECT_CLOCKS_DIR overrides
+        self.path = os.path.join(os.environ.get("ECT_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"ect_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

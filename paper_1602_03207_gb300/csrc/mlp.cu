@@ -2,7 +2,7 @@
 // linear output) trained and evaluated with tcgen05 tensor-core GEMMs
 // (bf16 operands, fp32 accumulation in TMEM) and an Adam optimiser with fp32
 // master weights.  It maps deposit parameters to the Delta Z signal along the
-// probe path; the solver is its data source and the judge of its error.
+// probe path; the solver is its data source and the reference for its error.
 //
 // Per training step: 5 forward GEMMs (epilogue: bias, SiLU, bf16 copies of
 // the activations in the two layouts the backward pass consumes), the loss

@@ -1,7 +1,8 @@
 """Delta Z surrogate: dataset generation with the solver, tcgen05 training, evaluation.
 
 Host-side orchestration only: every solve, every Delta Z and every training
-step runs in libect.so.  The solver is the data source and the judge:
+step runs in libect.so.  The solver is the data source and the reference
+for the surrogate's error:
 
 * dataset: for each seeded deposit (thickness, axial length, conductivity,
   relative permeability, azimuthal coverage, axial centre) the defect matrix

@@ -2,7 +2,7 @@
 
 The solver generates Delta Z_11 signals (128 probe positions) for seeded
 deposits on a small tube mesh; the tcgen05 MLP is trained on most of them and
-judged by the solver on the held-out rest.  Gain: one surrogate evaluation is
+checked against the solver on the held-out rest.  Gain: one surrogate evaluation is
 orders of magnitude faster than the solves it replaces, at an error well
 below that of the best input-independent predictor (the mean signal).  The
 aggregate error ||pred - ref||_F / ||ref||_F over the held-out set is the

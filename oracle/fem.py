@@ -35,7 +35,8 @@ import scipy.sparse as sp
 
 
 def tet_geometry(xyz, tets):
-    """Volumes |K| (T,) and barycentric gradients g (T,4,3) of each tet.
+    """Volumes |K| (T,) and barycentric gradients g (T,4,3) of each tet (the P1 hat
+    functions of Sec. 3, Step 3).
 
     With J the 3x3 matrix whose rows are x_a - x_0 (a = 1..3), the
     barycentric coordinates satisfy x - x_0 = sum_a lambda_a (x_a - x_0), so
@@ -53,7 +54,8 @@ def tet_geometry(xyz, tets):
 
 
 def element_matrices(vol, g, sigma, nu, nu_tilde, omega, delta):
-    """Element matrices E[K, a, b, r, c] for tets K (complex128, (T,4,4,4,4)).
+    """Element matrices E[K, a, b, r, c] for tets K (complex128, (T,4,4,4,4)): the blocks
+    L11, L12, L21, L22 of the coupled form of Sec. 2 with the gauge penalty of Sec. 4.
 
     a, b are local nodes (test, trial), r, c components (row = test
     component, col = trial component), component 3 = V.  Blocks:
@@ -87,7 +89,8 @@ def element_matrices(vol, g, sigma, nu, nu_tilde, omega, delta):
 
 
 def effective_coefficients(sigma, nu, sigma_d, nu_d, which):
-    """Per-tet (sigma, nu) of the background ('vacuum') or 'defect' matrix.
+    """Per-tet (sigma, nu) of the background ('vacuum') or 'defect' matrix (the M_0 / M_d
+    pair of Eq. impedkl).
 
     The defect arrays use NaN for "same as background"."""
     sigma = np.asarray(sigma, dtype=np.float64)
@@ -102,14 +105,16 @@ def effective_coefficients(sigma, nu, sigma_d, nu_d, which):
 
 
 def conducting_nodes(n_nodes, tets, sigma):
-    """Boolean (N,): node touches at least one tet with sigma > 0."""
+    """Boolean (N,): node touches at least one tet with sigma > 0 (V lives on the conductor,
+    Sec. 2; reading in the module notes)."""
     c = np.zeros(n_nodes, dtype=bool)
     c[np.asarray(tets)[np.asarray(sigma) > 0.0].ravel()] = True
     return c
 
 
 def assemble_raw(xyz, tets, sigma, nu, nu_tilde, omega, delta, chunk=1 << 16):
-    """Scalar CSR sum of the element matrices (before boundary conditions)."""
+    """Scalar CSR sum of the element matrices (before boundary conditions): the assembly of
+    Sec. 3, Steps 3-4, done serially."""
     xyz = np.asarray(xyz, dtype=np.float64)
     tets = np.asarray(tets, dtype=np.int64)
     n = 4 * xyz.shape[0]
@@ -129,7 +134,8 @@ def assemble_raw(xyz, tets, sigma, nu, nu_tilde, omega, delta, chunk=1 << 16):
 
 
 def fixed_dofs(bc_mask, conducting):
-    """Dof indices eliminated by A.n = 0, and V dofs of non-conducting nodes."""
+    """Dof indices eliminated by A.n = 0 on the box faces (Sec. 2 boundary conditions), and
+    V dofs of non-conducting nodes."""
     bc = np.asarray(bc_mask, dtype=np.int64)
     N = bc.shape[0]
     node = np.arange(N)
@@ -183,5 +189,6 @@ def scaling(M):
 
 
 def scaled(M, t):
+    """S = diag(t) M diag(t) (the symmetric scaling of reading 14 in the design notes)."""
     D = sp.diags(t)
     return (D @ M @ D).tocsr()

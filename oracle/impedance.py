@@ -20,10 +20,12 @@ import numpy as np
 
 
 def z_emf(b_k, u_l, I_k, I_l, omega):
+    """Coil EMF impedance Z_kl = -(i omega / (I_k I_l)) b_k^T u_l (bilinear; module notes)."""
     return -(1j * omega / (I_k * I_l)) * (np.asarray(b_k) @ np.asarray(u_l))
 
 
 def delta_z_reciprocity(M0, Md, u0_k, ud_l, I_k, I_l, omega):
+    """Delta Z_kl by reciprocity (Eq. impedkl read as the discrete identity of the module notes)."""
     return (1j * omega / (I_k * I_l)) * (np.asarray(u0_k) @ ((Md - M0) @ np.asarray(ud_l)))
 
 

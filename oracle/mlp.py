@@ -20,14 +20,17 @@ SIZES = (6, 256, 256, 256, 256, 256)
 
 
 def sigmoid(z):
+    """Logistic function 1/(1 + exp(-z)) (building block of SiLU)."""
     return 1.0 / (1.0 + np.exp(-z))
 
 
 def silu(z):
+    """SiLU z * sigmoid(z), the hidden activation (reading: the activation is unspecified)."""
     return z * sigmoid(z)
 
 
 def silu_grad(z):
+    """d silu / dz = sigmoid(z) (1 + z (1 - sigmoid(z)))."""
     s = sigmoid(z)
     return s * (1.0 + z * (1.0 - s))
 
@@ -57,6 +60,7 @@ def forward(params, X):
 
 
 def loss(y, t):
+    """Mean squared error 1/(2 B D) sum (y - t)^2 (module notes)."""
     return 0.5 * np.mean((y - t) ** 2)
 
 
@@ -76,6 +80,7 @@ def backward(params, cache, y, t):
 
 
 def adam_init(params):
+    """Zero first and second moments and step 0 for Adam (Kingma & Ba)."""
     return {"t": 0, "m": [[np.zeros_like(W), np.zeros_like(b)] for W, b in params],
             "v": [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]}
 

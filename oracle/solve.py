@@ -27,10 +27,12 @@ import scipy.sparse.linalg as spla
 
 
 def dense_solve(M, b):
+    """LAPACK LU solve on the dense matrix (tiny meshes; the direct solve of Sec. 3, Step 5)."""
     return np.linalg.solve(M.toarray() if sp.issparse(M) else M, b)
 
 
 def superlu_solve(M, b):
+    """SuperLU solve, the paper's own solver family (Sec. 3, Step 5)."""
     lu = spla.splu(sp.csc_matrix(M))
     return lu.solve(np.asarray(b)), lu
 
@@ -54,6 +56,8 @@ def block_jacobi(S, block_of_node):
 
 
 def block_jacobi_apply(P, r):
+    """z = blockdiag(S_ss)^-1 r over the subdomain blocks (the partition of Sec. 3, Step 2,
+    used as a preconditioner)."""
     starts, stops, inv = P
     z = np.empty_like(r, dtype=np.complex128)
     for s, e, B in zip(starts, stops, inv):
@@ -207,6 +211,7 @@ def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000, se
 
 
 def node_graph_from_tets(n_nodes, tets):
+    """Node adjacency of the mesh (nodes sharing a tet), as sorted neighbour lists."""
     tets = np.asarray(tets, dtype=np.int64)
     r = np.repeat(tets, 4, axis=1).ravel()
     c = np.tile(tets, (1, 4)).ravel()
@@ -217,6 +222,8 @@ def node_graph_from_tets(n_nodes, tets):
 
 
 def greedy_aggregates(G, agg_size):
+    """Greedy aggregation: each unaggregated seed takes its unaggregated neighbours in
+    increasing order, at most agg_size nodes (multigrid reading in the design notes)."""
     G = sp.csr_matrix(G)
     G.sort_indices()
     n = G.shape[0]
@@ -277,6 +284,8 @@ def amg_setup(S, w0, node_agg0, G0, max_coarse_dofs=2048, agg_size=8):
 
 
 def amg_apply(levels, r, l=0, gamma=2):
+    """One W-cycle (gamma = 2, 1 above the coarsest level): block-Jacobi pre-smoothing,
+    coarse corrections, block-Jacobi post-smoothing (multigrid reading in the design notes)."""
     L = levels[l]
     if "inv" in L:
         return L["inv"] @ r
@@ -290,6 +299,8 @@ def amg_apply(levels, r, l=0, gamma=2):
 
 
 def near_null_weights(t, fixed_dofs):
+    """Tentative-prolongator weights: 1/t on free dofs (a constant unscaled field per
+    component), 0 on constrained ones."""
     w = 1.0 / np.asarray(t, dtype=np.float64)
     w[np.asarray(fixed_dofs)] = 0.0
     return w

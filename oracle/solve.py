@@ -109,29 +109,33 @@ def givens(a, b):
     return abs(a) / rho, ph * np.conj(b) / rho, ph * rho
 
 
-def cgs2(V, w, selective=False):
+def cgs2(V, w, selective=False, one_pass=False):
     """Orthogonalise w against the orthonormal columns of V twice (CGS2).
 
     Returns (h, w_new, beta) with h = coefficients accumulated over both
     passes (Hermitian inner product) and beta = ||w_new||.  With
     selective=True the second pass runs only when the first one removed more
     than half of ||w||^2 (||w_1||^2 < ||w_0||^2 / 2, the Daniel-Gragg-Kaufman-
-    Stewart test with eta = 1/sqrt(2))."""
+    Stewart test with eta = 1/sqrt(2)); with one_pass=True it never runs
+    (classical Gram-Schmidt, the usual GMRES default; reading 17 of the design
+    notes: the paper does not name its variant)."""
     n0 = np.vdot(w, w).real
     h1 = V.conj().T @ w
     w = w - V @ h1
-    if selective and np.vdot(w, w).real >= 0.5 * n0:
+    if one_pass or (selective and np.vdot(w, w).real >= 0.5 * n0):
         return h1, w, np.linalg.norm(w)
     h2 = V.conj().T @ w
     w = w - V @ h2
     return h1 + h2, w, np.linalg.norm(w)
 
 
-def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000, selective=False):
-    """Restarted right-preconditioned flexible GMRES.
+def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000, selective=False,
+           one_pass=False):
+    """Restarted right-preconditioned flexible GMRES (Saad).
 
     A and precond are callables (or matrices).  Stops when the true residual
     ||b - A x|| / ||b|| <= tol at a restart, or after maxiter iterations.
+    `selective` / `one_pass` choose the Gram-Schmidt variant (see cgs2).
     Returns (x, info) with info = dict(iters, relres, history)."""
     mv = A if callable(A) else (lambda v: A @ v)
     pc = (lambda v: v) if precond is None else (precond if callable(precond) else (lambda v: precond @ v))
@@ -163,7 +167,7 @@ def fgmres(A, b, precond=None, x0=None, tol=1e-10, restart=30, maxiter=10000, se
         for j in range(m):
             Z[:, j] = pc(V[:, j])
             w = mv(Z[:, j])
-            h, w, hn = cgs2(V[:, :j + 1], w, selective)
+            h, w, hn = cgs2(V[:, :j + 1], w, selective, one_pass)
             H[:j + 1, j] = h
             H[j + 1, j] = hn
             for i in range(j):                      # previous rotations

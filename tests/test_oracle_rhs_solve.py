@@ -292,6 +292,27 @@ def test_selective_reorthogonalisation():
     assert info["relres"] <= 1e-11
 
 
+def test_one_pass_gram_schmidt():
+    """One classical pass: h = V^H w exactly, w_new = w - V h, and the loss of orthogonality
+    is bounded by the cancellation (visible for a vector nearly inside span(V), removed by a
+    second pass); FGMRES with it still reaches the dense solution."""
+    rng = np.random.default_rng(9)
+    n, k = 300, 6
+    V, _ = np.linalg.qr(rng.normal(size=(n, k)) + 1j * rng.normal(size=(n, k)))
+    w = V @ (rng.normal(size=k) + 0j) + 1e-6 * (rng.normal(size=n) + 0j)
+    h, w1, beta = solve.cgs2(V, w, one_pass=True)
+    np.testing.assert_allclose(h, V.conj().T @ w, rtol=1e-13)
+    np.testing.assert_allclose(w1, w - V @ h, rtol=0, atol=1e-15 * np.linalg.norm(w))
+    assert beta == pytest.approx(np.linalg.norm(w1), rel=1e-14)
+    _, w2, _ = solve.cgs2(V, w)                                  # two passes: orthogonal to eps
+    assert np.abs(V.conj().T @ w2).max() <= np.abs(V.conj().T @ w1).max() + 1e-300
+    A = np.eye(40) * 4 + rng.normal(size=(40, 40)) + 1j * rng.normal(size=(40, 40))
+    b = rng.normal(size=40) + 1j * rng.normal(size=40)
+    x, info = solve.fgmres(A, b, tol=1e-12, restart=40, one_pass=True)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9)
+    assert info["relres"] <= 1e-12
+
+
 # ---------------------------------------------------------------- aggregation multigrid
 
 def _amg_case(shape=(7, 7, 9), which="vacuum"):

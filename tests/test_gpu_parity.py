@@ -92,6 +92,24 @@ def test_assembly_matches_oracle(ect, small):
         assert abs(G - G.T).max() <= 1e-13 * abs(G).max()
 
 
+def test_assembly_matches_oracle_large_gauge_penalty(ect):
+    """The V-gauge penalty (Sec. 4) at delta = 10 m^-2 instead of 1: the V-V
+    blocks of the conducting nodes change, the bound stays the same."""
+    import dataclasses
+    p = dataclasses.replace(small_problem(seed=2), delta=10.0)
+    ctx = ect.Context()
+    ctx.load_problem(p)
+    for w, wi in WHICH.items():
+        ctx.assemble(wi, ect.ECT_F64)
+        rp, col, val = ctx.matrix_copy(wi)
+        G = bsr_to_csr(rp, col, val)
+        O = fem.system_matrix(p, w)
+        d = np.sqrt(np.abs(O.diagonal()))
+        D = (G - O).tocoo()
+        assert np.all(np.abs(D.data) <= 1e-12 * d[D.row] * d[D.col] + 1e-300), w
+    ctx.close()
+
+
 def test_scaling_matches_oracle(ect, small):
     p, ctx, M = small
     for w, wi in WHICH.items():

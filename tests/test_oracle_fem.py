@@ -247,3 +247,74 @@ def test_skin_depth_decay():
         errs.append(np.abs(ax[sel] - exact[sel]).max())
     assert errs[-1] < 5e-3
     assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.5, errs
+
+
+def _scalar_p1_mass_quadrature(xyz, tets, weight):
+    """sum_K weight_K int_K l_a l_b by the 4-point rule (hat values = barycentric weights)."""
+    N = xyz.shape[0]
+    p = xyz[tets]
+    vol = np.abs(np.linalg.det(p[:, 1:] - p[:, :1])) / 6.0
+    loc = np.einsum("qa,qb->ab", QUAD4, QUAD4) / 4.0            # int l_a l_b / |K|
+    vals = (weight * vol)[:, None, None] * loc[None]
+    r = np.repeat(tets, 4, axis=1).ravel()
+    c = np.tile(tets, (1, 4)).ravel()
+    return sp.coo_matrix((vals.ravel(), (r, c)), shape=(N, N)).tocsr()
+
+
+def _weighted_p1_stiffness(xyz, tets, weight):
+    """sum_K weight_K |K| grad l_a . grad l_b with gradients from the 4x4 vertex matrix."""
+    N = xyz.shape[0]
+    rows, cols, vals = [], [], []
+    for t, wk in zip(tets, weight):
+        p = xyz[t]
+        G = hat_gradients_4x4(p)
+        v = abs(np.linalg.det(p[1:] - p[0])) / 6.0
+        K = wk * v * G @ G.T
+        for a in range(4):
+            for b in range(4):
+                rows.append(t[a]); cols.append(t[b]); vals.append(K[a, b])
+    return sp.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+
+
+@pytest.mark.parametrize("delta", [0.0, 1.0, 7.3e3])
+def test_gauge_penalty_block_closed_form(delta):
+    """V-V block of the coupled form with the gauge penalty of Sec. 4:
+    -(1/(i omega)) [K_sigma + delta M_sigma], where K_sigma and M_sigma are the
+    sigma-weighted P1 stiffness and mass matrices built here by independent
+    routes (4x4 vertex-matrix gradients, 4-point quadrature).  A dropped sigma,
+    a wrong mass weight (1/12 for 1/20) or delta on the stiffness fails it."""
+    m = small_mesh(shape=(4, 5, 4), jitter=0.15, seed=11)
+    rng = np.random.default_rng(4)
+    sig = rng.uniform(0.5e6, 2.0e6, m.n_tets)                    # tet-wise conductivity
+    om = 2 * math.pi * 1.0e5
+    M = fem.assemble_raw(m.xyz, m.tets, sig, np.zeros(m.n_tets), 0.0, om, delta)
+    V = 4 * np.arange(m.n_nodes) + 3
+    MVV = M[V][:, V].toarray()
+    K = _weighted_p1_stiffness(m.xyz, m.tets, sig).toarray()
+    Ms = _scalar_p1_mass_quadrature(m.xyz, m.tets, sig).toarray()
+    expect = -(1.0 / (1j * om)) * (K + delta * Ms)
+    assert np.abs(MVV - expect).max() <= 1e-13 * np.abs(expect).max()
+    # the penalty touches nothing but the V-V block
+    M0 = fem.assemble_raw(m.xyz, m.tets, sig, np.zeros(m.n_tets), 0.0, om, 0.0)
+    D = (M - M0).tocoo()
+    assert np.all(D.row % 4 == 3) and np.all(D.col % 4 == 3)
+
+
+def test_gauge_penalty_on_constant_potential():
+    """K 1 = 0, so a constant V is seen only through the penalty:
+    (M_VV 1)_a = -(delta/(i omega)) sum_{K ni a} sigma_K |K| / 4, and the total is
+    -(delta/(i omega)) int sigma (the lumped P1 mass, int l_a = |K|/4 per tet)."""
+    m = small_mesh(shape=(5, 4, 4), jitter=0.15, seed=12)
+    rng = np.random.default_rng(6)
+    sig = rng.uniform(0.5e6, 2.0e6, m.n_tets)
+    om, delta = 2 * math.pi * 3.0e4, 42.0
+    M = fem.assemble_raw(m.xyz, m.tets, sig, np.zeros(m.n_tets), 0.0, om, delta)
+    V = 4 * np.arange(m.n_nodes) + 3
+    y = M[V][:, V] @ np.ones(m.n_nodes)
+    p = m.xyz[m.tets]
+    vol = np.abs(np.linalg.det(p[:, 1:] - p[:, :1])) / 6.0
+    lumped = np.zeros(m.n_nodes)
+    np.add.at(lumped, m.tets.ravel(), np.repeat(sig * vol / 4.0, 4))
+    expect = -(delta / (1j * om)) * lumped
+    assert np.abs(y - expect).max() <= 1e-12 * np.abs(expect).max()
+    assert abs(y.sum() - (-(delta / (1j * om)) * (sig * vol).sum())) <= 1e-12 * abs(y.sum())

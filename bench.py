@@ -54,22 +54,20 @@ def load_peaks():
 
 
 def profiled_traffic(kernel, nnzb):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to nnzb blocks.
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json, scaled to nnzb blocks.
 
-    The summary (profiles/hot_kernels_midsize.md) records dram__bytes_read.sum +
-    dram__bytes_write.sum of one captured launch on the mid-size case and that case's nnzb in a
-    line "traffic `<kernel>`: <bytes> bytes at nnzb <n>"; traffic grows with the matrix (blocks
-    and the vectors of the same rows), so it is scaled by the ratio of block counts."""
-    import re
+    The record holds dram__bytes_read.sum + dram__bytes_write.sum of one captured launch on a
+    mid-size case and that case's nnzb; traffic grows with the matrix (blocks and the vectors of
+    the same rows), so it is scaled by the ratio of block counts.  None when the kernel has no
+    capture."""
     try:
-        with open(os.path.join(ROOT, "profiles", "hot_kernels_midsize.md")) as f:
-            for line in f:
-                m = re.match(r"traffic `(.+?)`: (\d+) bytes at nnzb (\d+)", line.strip())
-                if m and m.group(1) == kernel:
-                    return int(m.group(2)) * nnzb / int(m.group(3))
-    except OSError:
-        pass
-    return None
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    return rec["bytes"] * nnzb / rec["nnzb"]
 
 
 def dist_env():
@@ -196,7 +194,7 @@ def run_gpu(args):
     cur = [c.current for c in p.coils]
     base = ect.default_options(tol=args.tol, mode=ect.ECT_MODE_MIXED, restart=args.outer_restart,
                                inner_iters=args.inner_iters, max_iters=args.max_outer, use_graph=1,
-                               reorth=args.reorth)
+                               reorth=args.reorth, spmm_rows=args.spmm_rows)
     plain = ect.default_options(tol=args.tol, mode=ect.ECT_MODE_F64, restart=args.restart, use_graph=1,
                                 max_iters=args.max_iters)
     # device-resident sources: [P][2][n] (position-major, coil minor)
@@ -296,6 +294,8 @@ def run_gpu(args):
         return a0.elapsed_time(a1) / reps
 
     kk = min(k, 8)
+    ctx.set_spmm_rows(mixed.spmm_rows)
+    staged = mixed.spmm_rows != -1
     xs = torch.randn(kk, n, dtype=torch.complex64, device="cuda")
     ys = torch.empty_like(xs)
     spmv_ms = ktime(lambda: ctx.spmv(0, xs, ys, kk, precision=ect.ECT_F32))
@@ -305,7 +305,11 @@ def run_gpu(args):
     cgs_ms = ktime(lambda: ctx.cgs2(Vb, wv, precision=ect.ECT_F32), reps=5)
     del xs, ys, Vb, wv
     nrows = m.n_nodes
-    spmv_bytes = nnzb * (16 * 8 + 4) + 4 * (nrows + 1) + 2 * kk * n * 8
+    # matrix values and one column index per block (16-bit local index when staged, 32-bit
+    # otherwise), row pointers, x and y once per right-hand side (the staged kernel's tile lists,
+    # ~1 % of these bytes, are not counted)
+    spmv_bytes = nnzb * (16 * 8 + (2 if staged else 4)) + 4 * (nrows + 1) + 2 * kk * n * 8
+    kname = "k_spmm_pipe" if staged else "k_spmv_f32<8>"
     achieved = spmv_bytes / (spmv_ms / 1000.0) / 1e9
     peaks, src = load_peaks()
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
@@ -328,7 +332,7 @@ def run_gpu(args):
                                f"{P} probe positions per rank per step (= {4 * P} solves), tol {args.tol}",
                    "positions_per_step": P * world, "rhs_per_solve_call": k, "nnzb": nnzb,
                    "inner_iters": mixed.inner_iters, "outer_restart": mixed.restart,
-                   "reorth": mixed.reorth, "rhs_tile": mixed.rhs_tile,
+                   "reorth": mixed.reorth, "rhs_tile": mixed.rhs_tile, "spmm_rows": mixed.spmm_rows,
                    "l2": "inputs larger than L2 (matrices 3.8 GB FP64 / 1.9 GB FP32 each)",
                    "parallelism": f"positions sharded over {world} GPU(s)"},
         "clocks": clocks,
@@ -345,10 +349,10 @@ def run_gpu(args):
                        "cgs2_f32_j10_k1": cgs_ms},
         "setup_ms": {"mesh_gen_s": gen_s * 1000, "assemble": asm_ms, "precond": pc_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": profiled_traffic("k_spmv_f32<8>", nnzb) if kk == 8 else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the "
-                                       "53x53x120 case, scaled by nnzb (profiles/hot_kernels_midsize.md)",
-                     "kernel": f"k_spmv_f32<8> (SpMM, {kk} rhs)", "ms_per_launch": spmv_ms,
+                     "frac": achieved / hbm, "traffic": profiled_traffic(kname, nnzb) if kk == 8 else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on a "
+                                       "mid-size case, scaled by nnzb (profiles/traffic.json)",
+                     "kernel": f"{kname} (SpMM, {kk} rhs, spmm_rows {mixed.spmm_rows})", "ms_per_launch": spmv_ms,
                      "algorithmic_bytes": spmv_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"},
         "gpu_launches": int(launches),
     }
@@ -364,13 +368,11 @@ def run_gpu(args):
 # CPU oracle (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------
 
-def oracle_sample(args, budget_s=20.0, iters_per_solve=None, ips_src="the FP64 solve's iteration count"):
-    """Time the oracle's block-Jacobi FGMRES on a slab of the same workload.
+def oracle_setup(args):
+    """The oracle's FP64 system of a slab of the workload and its multigrid hierarchy.
 
     The slab keeps the full 53 x 53 cross-section and 40 node layers of the
-    z-range around the plate edge (same h, materials, jitter recipe);
-    seconds per iteration per unknown are measured and scaled to the full
-    4,000,016 unknowns and to the iterations one solve needs."""
+    z-range around the plate edge (same h, materials, jitter recipe)."""
     import ect_inputs as E
     from oracle import fem, rhs, solve
 
@@ -380,6 +382,7 @@ def oracle_sample(args, budget_s=20.0, iters_per_solve=None, ips_src="the FP64 s
     p = E.tsp_problem((shape[0], shape[1], nz), (lengths[0], lengths[1], Lz), jitter=jitter, z_pos=(0.0,))
     t0 = time.time()
     M = fem.system_matrix(p, "defect")
+    asm_s = time.time() - t0
     t = fem.scaling(M)
     S = fem.scaled(M, t)
     s1, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, "defect")
@@ -387,55 +390,123 @@ def oracle_sample(args, budget_s=20.0, iters_per_solve=None, ips_src="the FP64 s
     d, v = fem.fixed_dofs(p.mesh.bc_mask, cond)
     levels = solve.amg_setup(S, solve.near_null_weights(t, np.concatenate([d, v])), p.mesh.block_of_node,
                              solve.node_graph_from_tets(p.mesh.n_nodes, p.mesh.tets))
-    asm_s = time.time() - t0
+    setup_s = time.time() - t0
     b = fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, p.coils[0].as_tuple(), 0.0), p, "defect")
+    return {"S": S, "levels": levels, "rhs": t * b, "n_small": 4 * p.mesh.n_nodes,
+            "n_full": 4 * shape[0] * shape[1] * shape[2], "shape": (shape[0], shape[1], nz),
+            "assembly_s": asm_s, "setup_s": setup_s}
+
+
+def oracle_iterate(o, budget_s):
+    """FGMRES(30) iterations of the oracle for about budget_s seconds; (iterations, seconds)."""
+    from oracle import solve
     it = 0
-    t1 = time.time()
     x = None
+    t1 = time.time()
     while time.time() - t1 < budget_s:
-        x, info = solve.fgmres(S, t * b, lambda r: solve.amg_apply(levels, r), tol=1e-30, restart=30,
-                               maxiter=10, x0=x)
+        x, info = solve.fgmres(o["S"], o["rhs"], lambda r: solve.amg_apply(o["levels"], r), tol=1e-30,
+                               restart=30, maxiter=10, x0=x)
         it += info["iters"]
-    el = time.time() - t1
-    n_small = 4 * p.mesh.n_nodes
-    n_full = 4 * shape[0] * shape[1] * shape[2]
-    s_per_iter_dof = el / it / n_small
-    ips = iters_per_solve or 1000
-    solves_per_s = 1.0 / (s_per_iter_dof * n_full * ips)
-    return {"value": solves_per_s, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"oracle FP64 FGMRES(30) with its aggregation-multigrid W-cycle on a "
-                       f"{shape[0]}x{shape[1]}x{nz}-node slab of the workload ({n_small} dof): {it} iterations "
-                       f"in {el:.1f} s, scaled to {n_full} dof and {ips} iterations/solve ({ips_src}); "
-                       f"slab assembly + hierarchy {asm_s:.1f} s")}
+    return it, time.time() - t1
+
+
+def oracle_rate(o, it, el, ips):
+    """Full-size solves/s extrapolated from a sample: seconds per iteration per unknown, scaled
+    to the workload's unknowns and to ips iterations per solve."""
+    return 1.0 / (el / it / o["n_small"] * o["n_full"] * ips)
+
+
+def _superlu_child(shape, lengths, q):
+    import ect_inputs as E
+    from oracle import fem, rhs, solve
+    p = E.tsp_problem(shape, lengths, z_pos=(0.0,))
+    t0 = time.time()
+    M = fem.system_matrix(p, "defect")
+    t1 = time.time()
+    b = fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, p.coils[0].as_tuple(), 0.0), p, "defect")
+    _, lu = solve.superlu_solve(M, b)
+    t2 = time.time()
+    for _ in range(4):
+        lu.solve(b)
+    t3 = time.time()
+    q.put({"unknowns": 4 * p.mesh.n_nodes, "assembly_s": t1 - t0, "factor_s": t2 - t1, "solve_s": (t3 - t2) / 4})
+
+
+def superlu_leg(limit_s):
+    """SciPy SuperLU (the paper's solver family) on the oracle's matrix: a config-1-size mesh
+    measured, and the next size up attempted within limit_s seconds (child process, started
+    with spawn)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = []
+    for shape, lengths, lim in (((16, 16, 32), (30e-3, 30e-3, 60e-3), 10 * limit_s),
+                                ((20, 20, 40), (30e-3, 30e-3, 60e-3), limit_s)):
+        q = ctx.Queue()
+        pr = ctx.Process(target=_superlu_child, args=(shape, lengths, q))
+        t0 = time.time()
+        pr.start()
+        pr.join(lim)
+        if pr.is_alive():
+            pr.terminate()
+            pr.join()
+            out.append({"mesh": "x".join(map(str, shape)), "unknowns": 4 * shape[0] * shape[1] * shape[2],
+                        "completed": False, "note": f"did not complete in {lim:.0f} s"})
+        else:
+            r = q.get() if not q.empty() else {}
+            out.append(dict(r, mesh="x".join(map(str, shape)), completed=bool(r),
+                            wall_s=time.time() - t0,
+                            solves_per_s=(1.0 / r["solve_s"]) if r.get("solve_s") else None))
+    return out
 
 
 def cpu_baseline(args, stats):
     ips = None
     if stats.get("plain"):
         ips = stats["plain"].get("iters") or None
-    return oracle_sample(args, budget_s=args.cpu_budget, iters_per_solve=ips or args.ref_iters,
-                         ips_src="the GPU FP64 run's count" if ips else
-                         "iterations of the FP64 solve at this size, measured on a GB300")
+    ips = ips or args.ref_iters
+    o = oracle_setup(args)
+    it, el = oracle_iterate(o, args.cpu_budget)
+    rec = {"value": oracle_rate(o, it, el, ips), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"oracle FP64 FGMRES(30) with its aggregation-multigrid W-cycle on a "
+                      f"{'x'.join(map(str, o['shape']))}-node slab of the workload ({o['n_small']} unknowns): "
+                      f"{it} iterations in {el:.1f} s, scaled to {o['n_full']} unknowns and {ips} iterations per "
+                      f"solve ({'the GPU FP64 run' if stats.get('plain') else 'the FP64 count at this size'}); "
+                      f"slab assembly {o['assembly_s']:.1f} s, assembly + hierarchy {o['setup_s']:.1f} s"),
+           "oracle_assembly": {"unknowns": o["n_small"], "seconds": o["assembly_s"]}}
+    if args.superlu_limit > 0:
+        rec["superlu"] = superlu_leg(args.superlu_limit)
+    return rec
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores.  Each step is one
+    timed sample of FGMRES iterations on the slab (ms_per_step is that measured time); the
+    value is the full-size rate extrapolated from the samples."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     t0 = time.time()
-    vals = []
+    o = oracle_setup(args)
+    samples = []
     for _ in range(args.warmup + args.steps):
-        vals.append(oracle_sample(args, budget_s=args.ref_budget, iters_per_solve=args.ref_iters,
-                                  ips_src="iterations of the FP64 solve at this size, measured on a GB300"))
-    v = vals[-args.steps:]
-    value = statistics.median([x["value"] for x in v])
+        samples.append(oracle_iterate(o, args.ref_budget))
+    v = samples[-args.steps:]
+    rates = [oracle_rate(o, it, el, args.ref_iters) for it, el in v]
+    value = statistics.median(rates)
+    ms = 1000.0 * sum(el for _, el in v) / len(v)
+    sample = (f"per step: {statistics.median([it for it, _ in v])} oracle FGMRES(30) iterations (multigrid W-cycle) "
+              f"on a {'x'.join(map(str, o['shape']))}-node slab of the workload ({o['n_small']} unknowns), "
+              f"{ms / 1000:.1f} s; value extrapolated to {o['n_full']} unknowns and {args.ref_iters} iterations "
+              f"per solve (the FP64 count at this size on a GB300); setup {o['setup_s']:.1f} s")
     rec = {"impl": "reference", "metric": "probe solves/s at 4M complex DOF, FP64 plain vs mixed+batched, "
            "dZ err<=1e-6", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 4 * args.positions * 1000.0 / value,
+           "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_basis": "measured wall time of one oracle sample",
+           "value_basis": "extrapolated from the timed samples",
            "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded, ect_inputs)",
            "config": {"workload": f"{args.config} (oracle sample)"},
-           "cpu_baseline": dict(v[-1], value=value),
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": time.time() - t0}
     print(json.dumps(rec))
@@ -533,6 +604,8 @@ def main():
     ap.add_argument("--max-outer", type=int, default=400)
     ap.add_argument("--inner-iters", type=int, default=20)
     ap.add_argument("--reorth", type=int, default=1, help="Gram-Schmidt variant when not autotuned (0-3)")
+    ap.add_argument("--spmm-rows", type=int, default=0,
+                    help="FP32 SpMM row tiling when not autotuned (0 auto, -1 unstaged)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel-probe", action="store_true", help="only launch the hot kernels on a mid-size case")
     ap.add_argument("--probe-mg", action="store_true")
@@ -540,6 +613,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--superlu-limit", type=float, default=60.0,
+                    help="seconds allowed for the SuperLU attempt at 64,000 unknowns (0: skip the SuperLU leg)")
     ap.add_argument("--ref-budget", type=float, default=10.0)
     ap.add_argument("--ref-iters", type=int, default=1410)
     args = ap.parse_args()

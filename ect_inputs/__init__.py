@@ -212,6 +212,108 @@ def box_mesh(shape, lengths, block_shape=(2, 2, 4), jitter=0.0, seed=0):
                 lengths=tuple(lengths))
 
 
+def delaunay_box_mesh(shape, lengths, jitter=0.35, seed=0, block_nodes=8):
+    """Unstructured tetrahedral mesh of the box: the nodes of an nx x ny x nz
+    grid moved by U[-jitter*h, jitter*h] per axis (interior nodes freely, face
+    nodes within their face, edge nodes along their edge, corners fixed, so
+    the box faces stay planar), re-triangulated by Delaunay (scipy's Qhull)
+    and oriented positively.  No tet is a Kuhn tet and node valences vary.
+
+    The nodes keep the grid's lexicographic order and block_of_node is a
+    placeholder (consecutive runs of block_nodes nodes); a partitioner
+    assigns the real subdomains and node order (see permute_mesh)."""
+    from scipy.spatial import Delaunay
+
+    base = box_mesh(shape, lengths, (1, 1, 1), jitter=0.0)
+    nx, ny, nz = shape
+    n = nx * ny * nz
+    # box_mesh with 1x1x1 blocks numbers nodes x-fastest, so node id = grid index
+    xyz = base.xyz.copy()
+    h = np.array(lengths, dtype=np.float64) / (np.array(shape) - 1)
+    on = [(base.bc_mask & bit) != 0 for bit in (BC_AX, BC_AY, BC_AZ)]
+    nfaces = on[0].astype(int) + on[1].astype(int) + on[2].astype(int)
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-jitter, jitter, size=(n, 3)) * h[None, :]
+    for a in range(3):
+        movable = (nfaces == 0) | ((nfaces >= 1) & (nfaces <= 2) & ~on[a])
+        xyz[:, a] += np.where(movable, d[:, a], 0.0)
+    tets = Delaunay(xyz).simplices.astype(np.int64)
+    vol = tet_volumes(xyz, tets)
+    flip = vol < 0.0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    if np.any(np.abs(vol) <= 1e-9 * float(np.prod(h))):
+        raise ValueError("degenerate tetrahedron in the Delaunay mesh (change the seed)")
+    block = (np.arange(n) // block_nodes).astype(np.int32)
+    return Mesh(xyz=xyz, tets=tets.astype(np.int32), block_of_node=block, bc_mask=base.bc_mask.copy(),
+                shape=tuple(shape), block_shape=(block_nodes,), lengths=tuple(lengths))
+
+
+def permute_mesh(mesh, new_id, block_of_new):
+    """The same mesh with node i renamed new_id[i]; block_of_new gives the
+    subdomain of each renamed node (non-decreasing).  Tets keep their order."""
+    new_id = np.asarray(new_id, dtype=np.int64)
+    n = mesh.n_nodes
+    if np.sort(new_id).tolist() != list(range(n)):
+        raise ValueError("new_id is not a permutation")
+    xyz = np.empty_like(mesh.xyz)
+    xyz[new_id] = mesh.xyz
+    bc = np.empty_like(mesh.bc_mask)
+    bc[new_id] = mesh.bc_mask
+    return Mesh(xyz=xyz, tets=new_id[mesh.tets].astype(np.int32),
+                block_of_node=np.asarray(block_of_new, dtype=np.int32), bc_mask=bc, shape=mesh.shape,
+                block_shape=mesh.block_shape, lengths=mesh.lengths)
+
+
+def write_tetgen(prefix, mesh, region=None):
+    """Write the mesh in TetGen's documented text format: prefix.node (index,
+    x, y, z, boundary marker = the A.n = 0 bit mask) and prefix.ele (index,
+    four node indices, optional region attribute), indices from 0."""
+    n, t = mesh.n_nodes, mesh.n_tets
+    with open(prefix + ".node", "w") as f:
+        f.write(f"{n} 3 0 1\n")
+        for i in range(n):
+            x, y, z = (float(v) for v in mesh.xyz[i])
+            f.write(f"{i} {x!r} {y!r} {z!r} {int(mesh.bc_mask[i])}\n")
+    with open(prefix + ".ele", "w") as f:
+        f.write(f"{t} 4 {0 if region is None else 1}\n")
+        for k in range(t):
+            a, b, c, d = (int(v) for v in mesh.tets[k])
+            tail = "" if region is None else f" {int(region[k])}"
+            f.write(f"{k} {a} {b} {c} {d}{tail}\n")
+
+
+def read_tetgen(prefix):
+    """Read prefix.node / prefix.ele (TetGen text format; '#' comments, first
+    index 0 or 1, optional point attributes and boundary marker, optional
+    tet region attribute).  Returns (xyz (N,3), tets (T,4) 0-based, bc marker
+    (N,) or None, region (T,) or None)."""
+    def rows(path):
+        out = []
+        with open(path) as f:
+            for line in f:
+                line = line.split("#", 1)[0].split()
+                if line:
+                    out.append(line)
+        return out
+
+    nrows = rows(prefix + ".node")
+    n, dim, nattr, nbm = (int(v) for v in nrows[0][:4])
+    if dim != 3:
+        raise ValueError("3-D points expected")
+    pts = nrows[1:1 + n]
+    first = int(pts[0][0])
+    xyz = np.array([[float(v) for v in r[1:4]] for r in pts])
+    bc = np.array([int(r[4 + nattr]) for r in pts], dtype=np.int64) if nbm else None
+    erows = rows(prefix + ".ele")
+    t, npt, nreg = (int(v) for v in erows[0][:3])
+    if npt != 4:
+        raise ValueError("linear tetrahedra (4 nodes) expected")
+    ele = erows[1:1 + t]
+    tets = np.array([[int(v) - first for v in r[1:5]] for r in ele], dtype=np.int64)
+    region = np.array([float(r[5]) for r in ele]) if nreg else None
+    return xyz, tets, bc, region
+
+
 def tet_volumes(xyz, tets):
     """Signed volumes (used only to validate generated meshes)."""
     p = xyz[tets]
@@ -309,13 +411,14 @@ CONFIGS = {
 
 
 def wall_loss_problem(shape, lengths, block_shape=(2, 2, 4), jitter=0.0, seed=0,
-                      z_pos=(0.0,), sigma_d=0.5e6, name=""):
+                      z_pos=(0.0,), sigma_d=0.5e6, name="", mesh=None):
     """Tube in water with a wall-loss patch as the defect (configs 1 and 3).
 
     Omega_d = tube-wall tets with centroid z in [-2, 2] mm and polar angle in
-    [0, pi/2]; there the conductivity drops from 1e6 to sigma_d.
+    [0, pi/2]; there the conductivity drops from 1e6 to sigma_d.  `mesh`
+    replaces the structured mesh (e.g. delaunay_box_mesh of the same box).
     """
-    m = box_mesh(shape, lengths, block_shape, jitter, seed)
+    m = mesh if mesh is not None else box_mesh(shape, lengths, block_shape, jitter, seed)
     c = centroids(m)
     tube = tube_tets(c)
     sigma = np.where(tube, SIGMA_TUBE, 0.0)

@@ -77,6 +77,8 @@ typedef struct {
                            first removed more than half of ||w||^2 (default); 2: as 1 in
                            the FP64 loop, one classical pass in the mixed mode's FP32 loop;
                            3: one classical pass in both loops                           */
+    int spmm_rows;      /* FP32 SpMM row tiling: block rows per shared-memory-staged tile
+                           (0 = auto, 16); -1 = the unstaged kernels (x gathered from L1/L2) */
 } ect_options;
 
 typedef struct {
@@ -92,7 +94,7 @@ typedef struct {
 
 /* Fill *opt with defaults: tol 1e-10, restart 30, max_iters 20000, F64 mode,
  * inner_iters 30, graphs on, automatic rhs tile, no timeout, selective
- * reorthogonalisation. */
+ * reorthogonalisation, staged FP32 SpMM with automatic row tiling. */
 void ect_default_options(ect_options* opt);
 
 /* Create a context bound to a CUDA stream (a cudaStream_t, may be NULL for the
@@ -123,11 +125,39 @@ int ect_set_mesh(ect_ctx* ctx, const double* h_xyz, int64_t n_nodes,
                  const double* h_sigma_d, const double* h_nu_d,
                  const int32_t* h_block_of_node, const uint8_t* h_bc_mask);
 
+/* Step 2 of Sec. 3 for meshes that come without a partition (e.g. from a
+ * mesh generator): recursive coordinate bisection of the nodes into
+ * subdomains of at most max_block_nodes (1..16) nodes.
+ *   h_xyz           double[n_nodes][3] node coordinates
+ *   h_new_id        int32[n_nodes] out: new index of node i
+ *   h_block_of_new  int32[n_nodes] out: subdomain of new node j, non-decreasing
+ *                   from 0 in steps of 0 or 1 (the order ect_set_mesh needs)
+ * Relabel the mesh with h_new_id (tets, coordinates, per-node arrays) before
+ * ect_set_mesh.  Host-only, deterministic, needs no context (errors:
+ * ect_last_error(NULL)). */
+int ect_partition(const double* h_xyz, int64_t n_nodes, int max_block_nodes, int32_t* h_new_id,
+                  int32_t* h_block_of_new);
+
 /* Replace the defect configuration (h_sigma_d, h_nu_d as in ect_set_mesh;
  * NaN = background, NULL = no defect) on the current mesh without rebuilding
  * the pattern: the defect matrix and its preconditioner must be assembled
  * and set up again.  Used to scan many deposits on one mesh. */
 int ect_set_defect(ect_ctx* ctx, const double* h_sigma_d, const double* h_nu_d);
+
+/* Impedance boundary condition (Sec. 2, Eq. IBC with the surface integral of
+ * Eq. ibcROTA) for configuration `which`: the tets with h_tet_plate[t] != 0
+ * (a good conductor, e.g. the support plate, of conductivity sigma_p and
+ * reluctivity nu_p = 1/mu_p) are removed from the volume forms, every dof of
+ * a node that touches only plate tets is fixed to zero, and on the plate's
+ * surface (faces shared with the remaining tets, normal n into the plate)
+ * the A-A block receives -(i omega / Z) int A_tau . Phi_tau with
+ * Z = (1 - i)/(delta sigma_p), delta = sqrt(2 nu_p / (omega sigma_p)) at the
+ * frequency of the next ect_assemble.  h_tet_plate: uint8[n_tets] (host,
+ * copied); NULL clears the condition.  The matrix and preconditioner of
+ * `which` must be assembled and set up again.  With the condition set,
+ * Delta Z is the coil-EMF difference (ect_delta_z needs d_b; ect_impedance
+ * does this itself).  ect_set_defect clears a condition set on ECT_DEFECT. */
+int ect_set_ibc(ect_ctx* ctx, int which, const uint8_t* h_tet_plate, double sigma_p, double nu_p);
 
 /* Frequency (Hz), nu_tilde = 1/mu_tilde of the Coulomb-gauge penalty (Eq. CGCdiv
  * text) and the V-gauge penalty factor delta of Sec. 4 (1/m^2). */
@@ -170,12 +200,21 @@ int ect_matrix_copy(ect_ctx* ctx, int which, int32_t* h_row_ptr, int32_t* h_col,
 /* Copy the scaling vector t (double[4*n_nodes]), S = diag(t) M diag(t). */
 int ect_scaling_copy(ect_ctx* ctx, int which, double* h_t);
 
-/* y = M x for k vectors (unscaled matrix, FP64; or the FP32 copy of the
- * unscaled matrix when precision == ECT_F32, in which case d_x, d_y are
- * complex64).  d_x, d_y: [k][n_nodes][4], must not overlap. */
+/* y = M x for k vectors (unscaled matrix, FP64), or y = S x with the FP32
+ * copy of the scaled matrix S = T M T when precision == ECT_F32 (d_x, d_y
+ * complex64; the shared-memory-staged kernel with the default row tiling).
+ * d_x, d_y: [k][n_nodes][4], must not overlap. */
 int ect_spmv(ect_ctx* ctx, int which, int precision, const void* d_x, void* d_y, int k);
 
-/* z = blockdiag(S_ss)^-1 r on the scaled system for k vectors ([k][n][4]). */
+/* Row tiling of the shared-memory-staged FP32 SpMM used by the kernel-level
+ * calls ect_spmv (ECT_F32) and ect_precond_apply (ECT_F32, multigrid
+ * preconditioner): rows block rows per tile (0 = auto, 16; at most 64);
+ * -1 = the unstaged kernels.  Solves take ect_options.spmm_rows instead. */
+int ect_set_spmm_rows(ect_ctx* ctx, int rows);
+
+/* z = P^-1 r on the scaled system for k vectors ([k][n][4]): the
+ * preconditioner set up by ect_precond_setup (subdomain blocks, two-level or
+ * multigrid W-cycle). */
 int ect_precond_apply(ect_ctx* ctx, int which, int precision, const void* d_r, void* d_z, int k);
 
 /* Classical Gram-Schmidt applied twice (the Arnoldi step of GMRES):
@@ -218,7 +257,9 @@ int ect_autotune(ect_ctx* ctx, int which, const void* d_rhs, void* d_work, int k
  * 1 and 2 solutions of the vacuum and defect systems); h_current[2] the coil
  * currents; h_dz receives complex128 [2][2].  If h_dz_emf is not NULL it
  * receives the coil-EMF difference -(i omega/(I_k I_l)) b_k^T (u_l^d - u_l^0)
- * computed from d_b (complex128 [2][n_nodes][4]) as a cross-check. */
+ * computed from d_b (complex128 [2][n_nodes][4]) as a cross-check.  With an
+ * impedance boundary condition (ect_set_ibc) h_dz receives the EMF form and
+ * d_b is required. */
 int ect_delta_z(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_b,
                 const double* h_current, double* h_dz, double* h_dz_emf);
 
@@ -232,8 +273,10 @@ int ect_delta_z(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_
  * Scratch: a static device array of 2.1 MB holding partial sums for at most
  * 64 positions (n_pos > 64 returns ECT_ERR_ARG); every GPU that loads the
  * library keeps it until the process exits.  The first call on a device looks
- * up the array's device address (with that device current); make that first
- * call before any stream capture.  All calls share the array: calls that
+ * up the array's device address (with that device current) and keeps it for
+ * the life of the process; make that first call before any stream capture.
+ * cudaDeviceReset invalidates the kept address: do not call this function
+ * on a device after resetting it.  All calls share the array: calls that
  * overlap on the GPU race.  Synchronises the context stream. */
 int ect_delta_z_static(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_b, const double* h_current,
                        int n_pos, double* h_dz, double* h_dz_emf);
@@ -244,6 +287,40 @@ int ect_delta_z_static(ect_ctx* ctx, const void* d_u0, const void* d_ud, const v
  * Needs both matrices assembled and their preconditioners set up. */
 int ect_impedance(ect_ctx* ctx, const ect_coil coils[2], const double* h_z_pos, int n_pos,
                   const ect_options* opt, double* h_dz, ect_stats* stats);
+
+/* ---- frequency sweeps (frequency as a batch dimension) ---------------------
+ * Eq. impedmod's signals are read over frequency; the matrices of both
+ * configurations change with omega (the -i omega sigma mass term, the
+ * -(sigma / (i omega)) V terms and an impedance boundary condition) while
+ * the pattern, the coefficients and the constraints do not. */
+
+/* Matrix index of configuration `config` (ECT_VACUUM / ECT_DEFECT) at sweep
+ * frequency f; usable as `which` in ect_precond_setup, ect_matrix_copy,
+ * ect_scaling_copy, ect_spmv, ect_precond_apply and ect_solve. */
+#define ECT_SWEEP_MATRIX(f, config) (2 + 2 * (f) + (config))
+
+/* Assemble both configurations at n_freq (1..16) frequencies h_freq_hz (Hz)
+ * in one pass over the pattern per configuration (one kernel writes the
+ * n_freq value sets), with the context's coefficients, nu_tilde, delta and
+ * impedance boundary condition.  Replaces a previous sweep.  Each sweep
+ * matrix then needs ect_precond_setup.  ect_set_mesh, ect_set_physics,
+ * ect_set_defect and ect_set_ibc discard the sweep. */
+int ect_assemble_sweep(ect_ctx* ctx, const double* h_freq_hz, int n_freq, int precision_mask);
+
+/* Solve configuration `config` at every sweep frequency in one lockstep
+ * Krylov solve: d_rhs, d_x complex128 [n_freq][k][n_nodes][4] (block f uses
+ * the matrix of frequency f); k * n_freq <= 4096.  Options and statistics as
+ * for ect_solve (stats cover all n_freq * k right-hand sides). */
+int ect_solve_sweep(ect_ctx* ctx, int config, const void* d_rhs, void* d_x, int k, const ect_options* opt,
+                    ect_stats* stats);
+
+/* ect_impedance at every sweep frequency: h_dz receives complex128
+ * [n_freq][n_pos][2][2] (Delta Z at each frequency; Z_FA and Z_F3 of
+ * Eq. impedmod follow from it).  The coil sources are built once (they do
+ * not depend on the frequency) and both configurations are solved for all
+ * frequencies in lockstep. */
+int ect_impedance_sweep(ect_ctx* ctx, const ect_coil coils[2], const double* h_z_pos, int n_pos,
+                        const ect_options* opt, double* h_dz, ect_stats* stats);
 
 /* ---- surrogate MLP ----------------------------------------------------------
  * Not in the paper: a learned map from deposit parameters to the Delta Z

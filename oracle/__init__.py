@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, obviously correct
 restatement of what the method computes, written from the paper's equations
-(Sec. 2-3) and the readings listed in the design notes.  Only the test suite,
+(Sec. 2-3) and the readings stated in each module's notes (where the paper
+is silent, garbled or ambiguous).  Only the test suite,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 it.  It shares no code with the CUDA library and never imports it; the two
 meet only in the seeded input generator ``ect_inputs``.

@@ -189,6 +189,9 @@ def scaling(M):
 
 
 def scaled(M, t):
-    """S = diag(t) M diag(t) (the symmetric scaling of reading 14 in the design notes)."""
+    """S = diag(t) M diag(t).  The paper does not say how residuals are measured; the
+    solver's gate is the relative residual of this symmetrically scaled system, because the
+    diagonal magnitudes of the A and V rows differ by ~1e5 and the unscaled norm hides the V
+    equations."""
     D = sp.diags(t)
     return (D @ M @ D).tocsr()

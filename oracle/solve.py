@@ -117,8 +117,8 @@ def cgs2(V, w, selective=False, one_pass=False):
     selective=True the second pass runs only when the first one removed more
     than half of ||w||^2 (||w_1||^2 < ||w_0||^2 / 2, the Daniel-Gragg-Kaufman-
     Stewart test with eta = 1/sqrt(2)); with one_pass=True it never runs
-    (classical Gram-Schmidt, the usual GMRES default; reading 17 of the design
-    notes: the paper does not name its variant)."""
+    (classical Gram-Schmidt, the usual GMRES default).  The paper names GMRES but
+    not its Gram-Schmidt variant, so all three are offered."""
     n0 = np.vdot(w, w).real
     h1 = V.conj().T @ w
     w = w - V @ h1
@@ -227,7 +227,8 @@ def node_graph_from_tets(n_nodes, tets):
 
 def greedy_aggregates(G, agg_size):
     """Greedy aggregation: each unaggregated seed takes its unaggregated neighbours in
-    increasing order, at most agg_size nodes (multigrid reading in the design notes)."""
+    increasing order, at most agg_size nodes.  The paper has no multigrid: this is the
+    coarse space built on its partition (Sec. 3, Step 2), as in the notes above."""
     G = sp.csr_matrix(G)
     G.sort_indices()
     n = G.shape[0]
@@ -289,7 +290,7 @@ def amg_setup(S, w0, node_agg0, G0, max_coarse_dofs=2048, agg_size=8):
 
 def amg_apply(levels, r, l=0, gamma=2):
     """One W-cycle (gamma = 2, 1 above the coarsest level): block-Jacobi pre-smoothing,
-    coarse corrections, block-Jacobi post-smoothing (multigrid reading in the design notes)."""
+    coarse corrections, block-Jacobi post-smoothing (the cycle defined in the notes above)."""
     L = levels[l]
     if "inv" in L:
         return L["inv"] @ r

@@ -29,10 +29,13 @@ int guarded(ect_ctx* c, F&& f) {
     }
 }
 
-void check_which(int which) {
-    ECT_REQUIRE(which == ECT_VACUUM || which == ECT_DEFECT, ECT_ERR_ARG, "which must be ECT_VACUUM or ECT_DEFECT");
+void check_which(const ect_ctx* c, int which) {
+    ECT_REQUIRE(which_valid(c, which), ECT_ERR_ARG,
+                "which must be ECT_VACUUM, ECT_DEFECT or a sweep matrix (ECT_SWEEP_MATRIX)");
 }
 }  // namespace
+
+int guarded_call(ect_ctx* c, const std::function<void()>& f) { return guarded(c, f); }
 
 extern "C" {
 
@@ -47,6 +50,7 @@ void ect_default_options(ect_options* o) {
     o->rhs_tile = 0;
     o->timeout_s = 0.0;
     o->reorth = 1;
+    o->spmm_rows = 0;
 }
 
 int ect_create(ect_ctx** out, void* stream) {
@@ -90,9 +94,18 @@ int ect_set_mesh(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* 
     });
 }
 
+int ect_partition(const double* xyz, int64_t n_nodes, int max_block_nodes, int32_t* new_id, int32_t* block_of_new) {
+    return guarded(nullptr, [&] { partition_rcb(xyz, n_nodes, max_block_nodes, new_id, block_of_new); });
+}
+
 int ect_set_defect(ect_ctx* c, const double* sigma_d, const double* nu_d) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] { set_defect(c, sigma_d, nu_d); });
+}
+
+int ect_set_ibc(ect_ctx* c, int which, const uint8_t* plate, double sigma_p, double nu_p) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] { set_ibc(c, which, plate, sigma_p, nu_p); });
 }
 
 int ect_set_physics(ect_ctx* c, double freq, double nu_tilde, double delta) {
@@ -106,6 +119,7 @@ int ect_set_physics(ect_ctx* c, double freq, double nu_tilde, double delta) {
         c->nu_tilde = nu_tilde;
         c->delta = delta;
         c->physics_set = true;
+        clear_sweep(c);
         for (int m = 0; m < 2; ++m) c->mat[m].assembled = c->mat[m].pc_f64 = c->mat[m].pc_f32 = false;
     });
 }
@@ -138,15 +152,16 @@ int ect_matrix_info(const ect_ctx* c, int64_t* n_rows, int64_t* nnzb) {
 int ect_matrix_copy(ect_ctx* c, int which, int32_t* h_row_ptr, int32_t* h_col, double* h_val) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {
-        check_which(which);
+        check_which(c, which);
         ECT_REQUIRE(c->mesh_set, ECT_ERR_STATE, "no mesh");
         cudaStream_t st = c->stream;
         if (h_row_ptr)
             ECT_CUDA(cudaMemcpyAsync(h_row_ptr, c->row_ptr.p, c->row_ptr.bytes, cudaMemcpyDeviceToHost, st));
         if (h_col) ECT_CUDA(cudaMemcpyAsync(h_col, c->col.p, c->col.bytes, cudaMemcpyDeviceToHost, st));
         if (h_val) {
-            ECT_REQUIRE(c->mat[which].assembled, ECT_ERR_STATE, "matrix not assembled");
-            ECT_CUDA(cudaMemcpyAsync(h_val, c->mat[which].val.p, c->mat[which].val.bytes, cudaMemcpyDeviceToHost, st));
+            Matrix& M = ctx_mat(c, which);
+            ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "matrix not assembled");
+            ECT_CUDA(cudaMemcpyAsync(h_val, M.val.p, M.val.bytes, cudaMemcpyDeviceToHost, st));
         }
         ECT_CUDA(cudaStreamSynchronize(st));
     });
@@ -155,10 +170,11 @@ int ect_matrix_copy(ect_ctx* c, int which, int32_t* h_row_ptr, int32_t* h_col, d
 int ect_scaling_copy(ect_ctx* c, int which, double* h_t) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {
-        check_which(which);
+        check_which(c, which);
         ECT_REQUIRE(h_t, ECT_ERR_ARG, "null h_t");
-        ECT_REQUIRE(c->mat[which].assembled, ECT_ERR_STATE, "matrix not assembled");
-        ECT_CUDA(cudaMemcpyAsync(h_t, c->mat[which].t.p, c->mat[which].t.bytes, cudaMemcpyDeviceToHost, c->stream));
+        Matrix& M = ctx_mat(c, which);
+        ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "matrix not assembled");
+        ECT_CUDA(cudaMemcpyAsync(h_t, M.t.p, M.t.bytes, cudaMemcpyDeviceToHost, c->stream));
         ECT_CUDA(cudaStreamSynchronize(c->stream));
     });
 }
@@ -166,26 +182,46 @@ int ect_scaling_copy(ect_ctx* c, int which, double* h_t) {
 int ect_spmv(ect_ctx* c, int which, int precision, const void* d_x, void* d_y, int k) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {
-        check_which(which);
+        check_which(c, which);
         ECT_REQUIRE(d_x && d_y && k >= 1 && k <= 65535, ECT_ERR_ARG, "bad spmv arguments");
         ECT_REQUIRE(d_x != d_y, ECT_ERR_ARG, "x and y must not overlap");
         const int64_t ld = 4 * c->n_nodes;
         if (precision == ECT_F64) spmv_f64(c, which, false, (const double2*)d_x, (double2*)d_y, k, ld, 0, nullptr);
-        else if (precision == ECT_F32) spmv_f32(c, which, (const float2*)d_x, (float2*)d_y, k, ld, 0, nullptr);
+        else if (precision == ECT_F32) {
+            c->staged_rows = c->kernel_rows;
+            staged_prepare(c, which);
+            spmv_f32(c, which, (const float2*)d_x, (float2*)d_y, k, ld, 0, nullptr);
+            ECT_REQUIRE(!staged_take_error(c->stream), ECT_ERR_TIMEOUT,
+                        "a bounded wait for a bulk copy expired in the staged SpMM");
+        }
         else throw EctError{ECT_ERR_ARG, "bad precision"};
+    });
+}
+
+int ect_set_spmm_rows(ect_ctx* c, int rows) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] {
+        ECT_REQUIRE(rows == -1 || (rows >= 0 && rows <= 64), ECT_ERR_ARG, "rows must be -1 or in [0, 64]");
+        c->kernel_rows = rows == 0 ? STAGED_ROWS_DEFAULT : rows;
     });
 }
 
 int ect_precond_apply(ect_ctx* c, int which, int precision, const void* d_r, void* d_z, int k) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {
-        check_which(which);
+        check_which(c, which);
         ECT_REQUIRE(d_r && d_z && k >= 1 && k <= 65535, ECT_ERR_ARG, "bad precond arguments");
         ECT_REQUIRE(d_r != d_z, ECT_ERR_ARG, "r and z must not overlap");
         const int64_t ld = 4 * c->n_nodes;
         coarse_scratch(c, which, k);
         if (precision == ECT_F64) precond_apply_f64(c, which, (const double2*)d_r, (double2*)d_z, k, ld, 0, nullptr);
-        else if (precision == ECT_F32) precond_apply_f32(c, which, (const float2*)d_r, (float2*)d_z, k, ld, 0, nullptr);
+        else if (precision == ECT_F32) {
+            c->staged_rows = c->kernel_rows;
+            staged_prepare(c, which);
+            precond_apply_f32(c, which, (const float2*)d_r, (float2*)d_z, k, ld, 0, nullptr);
+            ECT_REQUIRE(!staged_take_error(c->stream), ECT_ERR_TIMEOUT,
+                        "a bounded wait for a bulk copy expired in the staged SpMM");
+        }
         else throw EctError{ECT_ERR_ARG, "bad precision"};
     });
 }
@@ -217,12 +253,12 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
                  ect_options* best, ect_stats* stats) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {
-        check_which(which);
+        check_which(c, which);
         ECT_REQUIRE(d_rhs && d_work && best && k >= 1, ECT_ERR_ARG, "bad autotune arguments");
         ect_options o;
         if (base) o = *base;
         else ect_default_options(&o);
-        Matrix& M = c->mat[which];
+        Matrix& M = ctx_mat(c, which);
         ECT_REQUIRE(M.assembled && M.pc_f64, ECT_ERR_STATE, "assemble and set up the preconditioner first");
         const bool mixed = o.mode == ECT_MODE_MIXED;
         ECT_REQUIRE(!mixed || (M.has_f32 && M.pc_f32), ECT_ERR_STATE, "mixed mode needs the FP32 operators");
@@ -310,6 +346,94 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
         }
         *best = win;
         if (stats) *stats = wst;
+    });
+}
+
+int ect_assemble_sweep(ect_ctx* c, const double* freq_hz, int n_freq, int precision_mask) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] { assemble_sweep(c, freq_hz, n_freq, precision_mask); });
+}
+
+int ect_solve_sweep(ect_ctx* c, int config, const void* d_rhs, void* d_x, int k, const ect_options* opt,
+                    ect_stats* st) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] {
+        ect_options o;
+        if (opt) o = *opt;
+        else ect_default_options(&o);
+        solve_sweep(c, config, (const double2*)d_rhs, (double2*)d_x, k, o, st);
+    });
+}
+
+int ect_impedance_sweep(ect_ctx* c, const ect_coil coils[2], const double* h_z_pos, int n_pos,
+                        const ect_options* opt, double* h_dz, ect_stats* stats) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] {
+        ECT_REQUIRE(coils && h_z_pos && h_dz && n_pos >= 1, ECT_ERR_ARG, "bad impedance arguments");
+        const int F = (int)c->sweep_omega.size();
+        ECT_REQUIRE(F >= 1, ECT_ERR_STATE, "no frequency sweep assembled (ect_assemble_sweep)");
+        for (int m = 2; m < 2 + 2 * F; ++m)
+            ECT_REQUIRE(ctx_mat(c, m).assembled && ctx_mat(c, m).pc_f64, ECT_ERR_STATE,
+                        "set up the preconditioner of every sweep matrix first");
+        ect_options o;
+        if (opt) o = *opt;
+        else ect_default_options(&o);
+        const int64_t nvec = 4 * c->n_nodes;
+        size_t fr = 0, tot = 0;
+        ECT_CUDA(cudaMemGetInfo(&fr, &tot));
+        const int m = o.restart, mi = o.mode == ECT_MODE_MIXED ? o.inner_iters : 0;
+        const double per_rhs = (double)nvec * F * (16.0 * (2 * m + 8) + 8.0 * (mi + 2));
+        int chunk = (int)std::max(1.0, std::min<double>(n_pos, 0.5 * (double)fr / (2.0 * per_rhs)));
+        chunk = std::min(chunk, std::max(1, 2048 / (2 * F)));
+        DevBuf B, U0, Ud;
+        B.alloc(sizeof(double2) * nvec * 2 * chunk);            // sources: the same at every frequency
+        U0.alloc(sizeof(double2) * nvec * 2 * chunk * F);       // [F][2 chunk][4N]
+        Ud.alloc(U0.bytes);
+        const double cur[2] = {coils[0].J_e * (coils[0].r_out - coils[0].r_in) * coils[0].length,
+                               coils[1].J_e * (coils[1].r_out - coils[1].r_in) * coils[1].length};
+        ect_stats agg{};
+        std::vector<double> dz(8 * (size_t)chunk);
+        for (int p0 = 0; p0 < n_pos; p0 += chunk) {
+            const int np = std::min(chunk, n_pos - p0);
+            for (int cc = 0; cc < 2; ++cc) {
+                DevBuf tmp;
+                tmp.alloc(sizeof(double2) * nvec * np);
+                coil_rhs(c, coils[cc], h_z_pos + p0, np, tmp.as<double2>());
+                ECT_CUDA(cudaMemcpy2DAsync(B.as<double2>() + cc * nvec, 2 * nvec * sizeof(double2), tmp.p,
+                                           nvec * sizeof(double2), nvec * sizeof(double2), np,
+                                           cudaMemcpyDeviceToDevice, c->stream));
+            }
+            ect_stats s0{}, s1{};
+            int rc = ECT_OK;
+            for (int cfg = 0; cfg < 2; ++cfg) {
+                try {
+                    solve_sweep(c, cfg, B.as<double2>(), (cfg ? Ud : U0).as<double2>(), 2 * np, o, cfg ? &s1 : &s0,
+                                true);
+                } catch (const EctError& e) {
+                    if (e.code != ECT_ERR_NOT_CONVERGED) throw;
+                    rc = e.code;
+                }
+            }
+            for (int f = 0; f < F; ++f) {
+                const int64_t off = (int64_t)f * 2 * np * nvec;
+                delta_z(c, U0.as<double2>() + off, Ud.as<double2>() + off, B.as<double2>(), cur, np, dz.data(),
+                        nullptr, c->sweep_omega[f]);
+                for (int q = 0; q < np; ++q)
+                    for (int e = 0; e < 8; ++e) h_dz[((int64_t)f * n_pos + p0 + q) * 8 + e] = dz[(size_t)q * 8 + e];
+            }
+            agg.iters = std::max({agg.iters, s0.iters, s1.iters});
+            agg.outer_iters = std::max({agg.outer_iters, s0.outer_iters, s1.outer_iters});
+            agg.converged += s0.converged + s1.converged;
+            agg.restarts += s0.restarts + s1.restarts;
+            agg.relres_max = std::max({agg.relres_max, s0.relres_max, s1.relres_max});
+            agg.ms += s0.ms + s1.ms;
+            agg.launches += s0.launches + s1.launches + 4 + F;
+            if (rc != ECT_OK) {
+                if (stats) *stats = agg;
+                throw EctError{ECT_ERR_NOT_CONVERGED, "a probe solve did not reach the tolerance"};
+            }
+        }
+        if (stats) *stats = agg;
     });
 }
 

@@ -5,7 +5,10 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <cmath>
 #include <cstring>
+#include <deque>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -172,6 +175,47 @@ struct DevBuf {
 };
 
 // ----------------------------------------------------------------------------
+// staged FP32 SpMM (spmm_staged.cu): a BSR matrix cut into tiles of
+// consecutive block rows; each tile lists the distinct column nodes its
+// blocks touch, and every block stores its column as an index into that list
+// ----------------------------------------------------------------------------
+struct StagedPlan {
+    bool ok = false;       // false: some row alone exceeds the tile limits (use the unstaged kernels)
+    int rows = 0;          // target block rows per tile
+    int64_t n_rows = 0, n_tiles = 0;
+    int max_cols = 0, max_blocks = 0;  // over all tiles (they size the shared memory)
+    int max_meta = 0;      // bytes of the largest tile's metadata record
+    DevBuf tile_row;       // int32[n_tiles+1] first block row of each tile
+    DevBuf tile_cptr;      // int32[n_tiles+1] offsets into the tiles' column lists
+    DevBuf tile_meta_off;  // int32[n_tiles+1] offsets (16-byte units) of each tile's metadata record
+    DevBuf tile_meta;      // per tile: row offsets (int32, rows+1) and local column indices
+                           // (uint16 per block), padded to 16 bytes
+    DevBuf tile_cols;      // int32 column nodes of each tile's list (runs of consecutive nodes)
+    void reset() {
+        ok = false;
+        rows = 0;
+        n_rows = n_tiles = 0;
+        max_cols = max_blocks = max_meta = 0;
+        for (DevBuf* b : {&tile_row, &tile_cptr, &tile_meta_off, &tile_meta, &tile_cols}) b->release();
+    }
+};
+// Build the plan of a BSR pattern (host arrays) for tiles of about `rows`
+// block rows; columns index a space of n_cols nodes.
+void staged_plan_build(cudaStream_t st, StagedPlan& P, const std::vector<int32_t>& rp,
+                       const std::vector<int32_t>& col, int64_t n_rows, int64_t n_cols, int rows);
+// y[r] = A x[r] (b == nullptr) or y[r] = b[r] - A x[r] for k right-hand sides
+// (b may equal y: in-place t -= A x).  x has leading dimension ldx (column
+// space), b and y ldy (row space).  FP32 complex values, 16 per block.
+void bsr_spmm_staged_f32(cudaStream_t st, const StagedPlan& P, const int32_t* rp, const float2* val,
+                         const float2* x, int64_t ldx, const float2* b, float2* y, int64_t ldy, int k,
+                         const int* active);
+// Read and clear the flag that a staged kernel sets when its bounded wait on
+// a bulk copy expired (1 = expired).  Synchronises the stream.
+int staged_take_error(cudaStream_t st);
+// default target rows per tile of the staged SpMM
+constexpr int STAGED_ROWS_DEFAULT = 16;
+
+// ----------------------------------------------------------------------------
 // context
 // ----------------------------------------------------------------------------
 struct Multigrid;  // aggregation multigrid hierarchy (multigrid.cu)
@@ -179,6 +223,7 @@ struct Matrix;
 void mg_free(Matrix& M);
 
 struct Matrix {
+    double omega = 0.0;    // angular frequency of the assembled values
     bool assembled = false;
     bool has_f32 = false;
     bool pc_f64 = false, pc_f32 = false;
@@ -202,6 +247,17 @@ struct Matrix {
     DevBuf gpart;          // split-GEMV partial sums
     int64_t coarse_k = 0;
     std::vector<uint8_t> h_cond;  // conducting-node flags (host)
+    std::vector<uint8_t> h_fix;   // host copy of fixmask
+    std::vector<double> h_sigma, h_nu;  // per-tet coefficients of this configuration (host)
+    // impedance boundary condition (Eq. IBC): plate tets removed, surface term on their boundary
+    bool ibc = false;
+    double ibc_sigma = 0.0, ibc_nu = 0.0;  // plate conductivity and 1/mu
+    std::vector<uint8_t> h_void;  // per tet: 1 = plate (removed from the volume forms)
+    DevBuf tvoid;          // uint8[T]
+    DevBuf s_ptr;          // int32[nnzb+1] per block: range of its surface contributions
+    DevBuf s_ent;          // uint32 face<<4 | a<<2 | b
+    DevBuf s_geo;          // double[F][4]: area, unit normal into the plate
+    int64_t n_faces = 0;
     Multigrid* mg = nullptr;
     Matrix() = default;
     Matrix(const Matrix&) = delete;
@@ -214,6 +270,11 @@ struct Matrix {
         coarse_group = 0;
         coarse_k = 0;
         h_cond.clear();
+        h_fix.clear();
+        ibc = false;
+        h_void.clear();
+        n_faces = 0;
+        for (DevBuf* b : {&tvoid, &s_ptr, &s_ent, &s_geo}) b->release();
         for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &sval32lo, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
                           &agg_lo, &agg_hi, &zv, &zv32, &rc, &zc, &gpart})
             b->release();
@@ -256,6 +317,13 @@ struct ect_ctx {
     std::vector<uint8_t> h_bc;
     std::vector<double> h_sigma0, h_nu0;
     Matrix mat[2];
+    // frequency sweep: configuration c at sweep frequency f is smat[2 f + c] (which = 2 + 2 f + c)
+    std::vector<double> sweep_omega;
+    std::deque<Matrix> smat;
+    StagedPlan fine_plan;  // staged-SpMM tiling of the (shared) finest pattern
+    int staged_rows = STAGED_ROWS_DEFAULT;  // rows per staged tile of the FP32 SpMM; -1 = unstaged
+    int kernel_rows = STAGED_ROWS_DEFAULT;  // staged tiling used by ect_spmv / ect_precond_apply
+    int plan_gen = 0;      // bumped whenever a staged plan is rebuilt (captured graphs key on it)
     Workspace* ws = nullptr;
     // scratch
     DevBuf scratch;        // reduction partials etc.
@@ -264,11 +332,29 @@ struct ect_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
+// matrix `which`: 0 / 1 the two configurations at the context's frequency,
+// 2 + 2 f + c configuration c at sweep frequency f
+inline bool which_valid(const ect_ctx* c, int which) {
+    return which == ECT_VACUUM || which == ECT_DEFECT || (which >= 2 && which < 2 + (int)c->smat.size());
+}
+inline Matrix& ctx_mat(ect_ctx* c, int which) {
+    if (which == ECT_VACUUM || which == ECT_DEFECT) return c->mat[which];
+    if (which >= 2 && which < 2 + (int)c->smat.size()) return c->smat[which - 2];
+    throw EctError{ECT_ERR_ARG, "which must be ECT_VACUUM, ECT_DEFECT or a sweep matrix (ECT_SWEEP_MATRIX)"};
+}
+inline double ctx_omega(const ect_ctx* c, int which) {
+    return which >= 2 ? c->sweep_omega[(which - 2) / 2] : c->omega;
+}
+
 // shared scratch (partials) helper
 inline double* ctx_scratch(ect_ctx* c, size_t doubles) {
     c->scratch.ensure(doubles * sizeof(double));
     return c->scratch.as<double>();
 }
+
+// Run f and turn any exception into a status code and c->err (the message of
+// the last error); implemented in api.cu, used by every extern "C" entry point.
+int guarded_call(ect_ctx* c, const std::function<void()>& f);
 
 // ----------------------------------------------------------------------------
 // cross-file entry points (implemented in the .cu files)
@@ -277,11 +363,19 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
                 const double* sigma, const double* nu, const double* sigma_d, const double* nu_d,
                 const int32_t* block_of_node, const uint8_t* bc_mask);
 void set_defect(ect_ctx* c, const double* sigma_d, const double* nu_d);
+void set_ibc(ect_ctx* c, int which, const uint8_t* plate, double sigma_p, double nu_p);
+// per-tet coefficients, conducting nodes and constraint mask of configuration m (mesh_setup.cu)
+void upload_config(ect_ctx* c, int m, const std::vector<double>& s, const std::vector<double>& n);
+// recursive coordinate bisection into contiguous subdomains of at most s nodes (partition.cu)
+void partition_rcb(const double* xyz, int64_t n_nodes, int s, int32_t* new_id, int32_t* block_of_new);
 void assemble_matrix(ect_ctx* c, int which, int precision_mask);
 void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group);
 void coarse_scratch(ect_ctx* c, int which, int k);
 void mg_setup(ect_ctx* c, int which, bool f32);
 void mg_scratch(Matrix& M, int k);
+// (re)build the staged-SpMM plans of the finest pattern and of the multigrid
+// levels of `which` for c->staged_rows (no-op when they match); not capturable
+void staged_prepare(ect_ctx* c, int which);
 void mg_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld, int tile, const int* active);
 void mg_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld, int tile, const int* active);
 int mg_levels(const Matrix& M);
@@ -325,10 +419,18 @@ void dense_gemv(cudaStream_t st, const C<T>* einv, int64_t nc, const C<T>* r, C<
                 const int* active, C<T>* part);
 
 void coil_rhs(ect_ctx* c, const ect_coil& coil, const double* h_z, int k, double2* d_rhs);
+// omega: the angular frequency of the solutions (0: the context's)
 void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b, const double* cur,
-             int n_pos, double* h_dz, double* h_dz_emf);
+             int n_pos, double* h_dz, double* h_dz_emf, double omega = 0.0);
+// drop the frequency-sweep matrices (their coefficients changed)
+void clear_sweep(ect_ctx* c);
 void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const ect_options& opt,
            ect_stats* st);
+// all sweep frequencies of configuration `config` in one lockstep solve: rhs, x [F][k][4N]
+// (same_rhs: one rhs array [k][4N] serves every frequency)
+void solve_sweep(ect_ctx* c, int config, const double2* rhs, double2* x, int k, const ect_options& opt,
+                 ect_stats* st, bool same_rhs = false);
+void assemble_sweep(ect_ctx* c, const double* freq_hz, int n_freq, int precision_mask);
 void cgs2_entry(ect_ctx* c, int precision, const void* V, int j, int64_t n, void* w, double* h,
                 double* beta);
 void workspace_free(ect_ctx* c);

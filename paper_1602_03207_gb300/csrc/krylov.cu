@@ -651,8 +651,38 @@ void cgs2_step(ect_ctx* c, Workspace* w, const C<T>* V, int64_t vstride, int j, 
     ECT_CHECK_LAUNCH();
 }
 
+// The right-hand sides of a solve fall into groups, each with its own matrix
+// (one group for a plain solve; one per frequency for a frequency sweep).
+// The Krylov kernels treat all right-hand sides together; the operator and
+// the preconditioner are applied group by group.
+struct Group {
+    int which, r0, k;
+    int rhs_r0;  // first right-hand side of the group in the caller's rhs array
+};
+using Groups = std::vector<Group>;
+
+inline const int* goff(const int* a, const Group& g) { return a ? a + g.r0 : nullptr; }
+
+void g_precond_f32(ect_ctx* c, const Groups& G, const float2* r, float2* z, int64_t ld, int tile, const int* act) {
+    for (const Group& g : G)
+        precond_apply_f32(c, g.which, r + g.r0 * ld, z + g.r0 * ld, g.k, ld, tile, goff(act, g));
+}
+void g_spmv_f32(ect_ctx* c, const Groups& G, const float2* x, float2* y, int64_t ld, int tile, const int* act) {
+    for (const Group& g : G) spmv_f32(c, g.which, x + g.r0 * ld, y + g.r0 * ld, g.k, ld, tile, goff(act, g));
+}
+void g_spmv_df32(ect_ctx* c, const Groups& G, const float2* x, double2* y, int64_t ld, int tile, const int* act) {
+    for (const Group& g : G) spmv_df32(c, g.which, x + g.r0 * ld, y + g.r0 * ld, g.k, ld, tile, goff(act, g));
+}
+void g_precond_f64(ect_ctx* c, const Groups& G, const double2* r, double2* z, int64_t ld, int tile, const int* act) {
+    for (const Group& g : G)
+        precond_apply_f64(c, g.which, r + g.r0 * ld, z + g.r0 * ld, g.k, ld, tile, goff(act, g));
+}
+void g_spmv_f64(ect_ctx* c, const Groups& G, const double2* x, double2* y, int64_t ld, int tile, const int* act) {
+    for (const Group& g : G) spmv_f64(c, g.which, true, x + g.r0 * ld, y + g.r0 * ld, g.k, ld, tile, goff(act, g));
+}
+
 // inner FP32 GMRES: z (FP64, Z_j) ~= S^-1 v (FP64, V_j), fixed mi iterations
-void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2* z, int rhs_tile) {
+void inner_solve(ect_ctx* c, Workspace* w, const Groups& G, const double2* v, double2* z, int rhs_tile) {
     cudaStream_t st = c->stream;
     const int k = w->k, mi = w->mi;
     const int64_t n = w->n, ld = n, vs = n * k;
@@ -667,8 +697,8 @@ void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2*
         float2* Vj = V32 + (int64_t)j * vs;
         float2* Vn = V32 + (int64_t)(j + 1) * vs;
         float2* Zj = Z32 + (int64_t)j * vs;
-        precond_apply_f32(c, which, Vj, Zj, k, ld, rhs_tile, live_i);
-        spmv_f32(c, which, Zj, Vn, k, ld, rhs_tile, live_i);
+        g_precond_f32(c, G, Vj, Zj, ld, rhs_tile, live_i);
+        g_spmv_f32(c, G, Zj, Vn, ld, rhs_tile, live_i);
         cgs2_step<float>(c, w, V32, vs, j, Vn, ld, w->Hi.as<double2>(), mi, live_i, w->inner_one_pass);
         k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
             w->npart.as<double>(), w->G, k, j, mi, w->Hi.as<double2>(), w->csi.as<double>(), w->sni.as<double2>(),
@@ -689,7 +719,7 @@ void inner_solve(ect_ctx* c, Workspace* w, int which, const double2* v, double2*
 
 // one restart cycle (capturable): starts from R / rnorm, ends with Y updated,
 // R = Bh - S Y and rnorm
-void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
+void run_cycle(ect_ctx* c, Workspace* w, const Groups& G, int rhs_tile) {
     cudaStream_t st = c->stream;
     const int k = w->k, m = w->m;
     const int64_t n = w->n, ld = n, vs = n * k;
@@ -708,11 +738,11 @@ void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
         if (w->mode == ECT_MODE_MIXED) {
             // Z_j is the FP32 inner solution (U32) widened: its product with S is formed in
             // double-float arithmetic from the FP32 copy and remainder of S
-            inner_solve(c, w, which, Vj, Zj, rhs_tile);
-            spmv_df32(c, which, w->U32.as<float2>(), Vn, k, ld, rhs_tile, live);
+            inner_solve(c, w, G, Vj, Zj, rhs_tile);
+            g_spmv_df32(c, G, w->U32.as<float2>(), Vn, ld, rhs_tile, live);
         } else {
-            precond_apply_f64(c, which, Vj, Zj, k, ld, rhs_tile, live);
-            spmv_f64(c, which, true, Zj, Vn, k, ld, rhs_tile, live);
+            g_precond_f64(c, G, Vj, Zj, ld, rhs_tile, live);
+            g_spmv_f64(c, G, Zj, Vn, ld, rhs_tile, live);
         }
         cgs2_step<double>(c, w, V, vs, j, Vn, ld, w->H.as<double2>(), m, live, w->outer_one_pass);
         k_arnoldi_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(
@@ -725,7 +755,7 @@ void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
                                                 w->y.as<double2>());
     k_maxpy<double><<<vgrid(w), TPB, 0, st>>>(Z, vs, m, w->Y.as<double2>(), ld, n, w->y.as<double2>(), m + 1, -1.0,
                                               run, nullptr, w->G);
-    spmv_f64(c, which, true, w->Y.as<double2>(), w->R.as<double2>(), k, ld, rhs_tile, run);
+    g_spmv_f64(c, G, w->Y.as<double2>(), w->R.as<double2>(), ld, rhs_tile, run);
     k_residual<<<vgrid(w), TPB, 0, st>>>(w->Bh.as<double2>(), w->R.as<double2>(), ld, n, run, w->npart.as<double>(),
                                         w->G);
     k_norm_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(w->npart.as<double>(), w->G, k, run, w->rnorm.as<double>());
@@ -734,23 +764,31 @@ void run_cycle(ect_ctx* c, Workspace* w, int which, int rhs_tile) {
 
 }  // namespace
 
-void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const ect_options& opt, ect_stats* stats) {
-    ECT_REQUIRE(which == ECT_VACUUM || which == ECT_DEFECT, ECT_ERR_ARG, "bad which");
+namespace {
+
+void solve_groups(ect_ctx* c, const Groups& G, const double2* rhs, double2* x, int k, const ect_options& opt,
+                  ect_stats* stats) {
     ECT_REQUIRE(k >= 1 && k <= 4096, ECT_ERR_ARG, "k must be in [1, 4096]");
     ECT_REQUIRE(rhs && x, ECT_ERR_ARG, "null rhs or x");
     ECT_REQUIRE(opt.restart >= 1 && opt.restart <= 64, ECT_ERR_ARG, "restart must be in [1, 64]");
     ECT_REQUIRE(opt.tol >= 0.0 && opt.max_iters >= 1, ECT_ERR_ARG, "bad tol or max_iters");
     ECT_REQUIRE(opt.mode == ECT_MODE_F64 || opt.mode == ECT_MODE_MIXED, ECT_ERR_ARG, "bad mode");
-    Matrix& M = c->mat[which];
-    ECT_REQUIRE(M.assembled && M.pc_f64, ECT_ERR_STATE, "assemble and set up the preconditioner first");
     const int mi = opt.mode == ECT_MODE_MIXED ? opt.inner_iters : 0;
-    if (opt.mode == ECT_MODE_MIXED) {
-        ECT_REQUIRE(M.has_f32 && M.pc_f32, ECT_ERR_STATE, "mixed mode needs the FP32 matrix and preconditioner");
-        ECT_REQUIRE(mi >= 1 && mi <= 64, ECT_ERR_ARG, "inner_iters must be in [1, 64]");
+    if (opt.mode == ECT_MODE_MIXED) ECT_REQUIRE(mi >= 1 && mi <= 64, ECT_ERR_ARG, "inner_iters must be in [1, 64]");
+    for (const Group& g : G) {
+        ECT_REQUIRE(which_valid(c, g.which), ECT_ERR_ARG, "bad which");
+        Matrix& M = ctx_mat(c, g.which);
+        ECT_REQUIRE(M.assembled && M.pc_f64, ECT_ERR_STATE, "assemble and set up the preconditioner first");
+        if (opt.mode == ECT_MODE_MIXED)
+            ECT_REQUIRE(M.has_f32 && M.pc_f32, ECT_ERR_STATE, "mixed mode needs the FP32 matrix and preconditioner");
     }
     cudaStream_t st = c->stream;
+    ECT_REQUIRE(opt.spmm_rows >= -1 && opt.spmm_rows <= 64, ECT_ERR_ARG, "spmm_rows must be -1 or in [0, 64]");
+    c->staged_rows = opt.spmm_rows == 0 ? STAGED_ROWS_DEFAULT : opt.spmm_rows;
+    if (opt.mode == ECT_MODE_MIXED)
+        for (const Group& g : G) staged_prepare(c, g.which);
     ECT_CUDA(cudaEventRecord(c->ev0, st));
-    coarse_scratch(c, which, k);
+    for (const Group& g : G) coarse_scratch(c, g.which, g.k);
     Workspace* w = get_ws(c, k, opt.restart, mi, opt.mode);
     const bool in1 = opt.reorth >= 2, out1 = opt.reorth == 3;
     if (w->selective != (opt.reorth != 0) || w->inner_one_pass != in1 || w->outer_one_pass != out1) {
@@ -761,9 +799,10 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
         w->outer_one_pass = out1;
     }
     const int64_t n = w->n, ld = n;
-    const double* t = M.t.as<double>();
     // scaled right-hand side and its norms; Y = 0, R = Bh
-    k_diag_scale<<<dim3(ew_blocks(n, k), k), TPB, 0, st>>>(rhs, w->Bh.as<double2>(), t, ld, n);
+    for (const Group& g : G)
+        k_diag_scale<<<dim3(ew_blocks(n, g.k), g.k), TPB, 0, st>>>(rhs + g.rhs_r0 * ld, w->Bh.as<double2>() + g.r0 * ld,
+                                                                  ctx_mat(c, g.which).t.as<double>(), ld, n);
     ECT_CUDA(cudaMemsetAsync(w->Y.p, 0, sizeof(double2) * n * k, st));
     ECT_CUDA(cudaMemcpyAsync(w->R.p, w->Bh.p, sizeof(double2) * n * k, cudaMemcpyDeviceToDevice, st));
     k_norm_part<double><<<vgrid(w), TPB, 0, st>>>(w->Bh.as<double2>(), ld, n, nullptr, w->npart.as<double>(), w->G);
@@ -799,13 +838,14 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
         }
         ECT_CUDA(cudaMemcpyAsync(w->run.p, run.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
         if (graphs) {
-            auto key = std::make_tuple(which, opt.mode, opt.rhs_tile, 0, 0);
+            auto key = std::make_tuple(G[0].which + 1000 * (int)G.size(), opt.mode, opt.rhs_tile, c->staged_rows,
+                                       c->plan_gen);
             auto it = w->graphs.find(key);
             if (it == w->graphs.end()) {
                 cudaGraph_t gr;
                 ECT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 try {
-                    run_cycle(c, w, which, opt.rhs_tile);
+                    run_cycle(c, w, G, opt.rhs_tile);
                 } catch (...) {
                     cudaStreamEndCapture(st, &gr);
                     throw;
@@ -821,7 +861,7 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
             ECT_CUDA(cudaGraphLaunch(it->second.first, st));
             launches += (int64_t)it->second.second;
         } else {
-            run_cycle(c, w, which, opt.rhs_tile);
+            run_cycle(c, w, G, opt.rhs_tile);
         }
         ECT_CUDA(cudaMemcpyAsync(rnorm.data(), w->rnorm.p, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         ECT_CUDA(cudaMemcpyAsync(nit.data(), w->nit.p, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
@@ -845,7 +885,9 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
     }
     launches += 1;
     // x = T y
-    k_diag_scale<<<dim3(ew_blocks(n, k), k), TPB, 0, st>>>(w->Y.as<double2>(), x, t, ld, n);
+    for (const Group& g : G)
+        k_diag_scale<<<dim3(ew_blocks(n, g.k), g.k), TPB, 0, st>>>(w->Y.as<double2>() + g.r0 * ld, x + g.r0 * ld,
+                                                                  ctx_mat(c, g.which).t.as<double>(), ld, n);
     ECT_CHECK_LAUNCH();
     ECT_CUDA(cudaEventRecord(c->ev1, st));
     ECT_CUDA(cudaEventSynchronize(c->ev1));
@@ -869,10 +911,30 @@ void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const e
         stats->ms = ms;
         stats->launches = launches;
     }
+    if (opt.mode == ECT_MODE_MIXED && c->staged_rows > 0 && staged_take_error(st))
+        throw EctError{ECT_ERR_TIMEOUT, "a bounded wait for a bulk copy expired in the staged SpMM"};
     if (status != ECT_OK) {
         throw EctError{status, status == ECT_ERR_TIMEOUT ? "solve timed out" : "NaN/Inf in the Krylov recurrence"};
     }
     if (conv < k) throw EctError{ECT_ERR_NOT_CONVERGED, "tolerance not reached within max_iters"};
+}
+
+}  // namespace
+
+void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const ect_options& opt, ect_stats* stats) {
+    ECT_REQUIRE(which_valid(c, which), ECT_ERR_ARG, "bad which");
+    solve_groups(c, Groups{Group{which, 0, k, 0}}, rhs, x, k, opt, stats);
+}
+
+void solve_sweep(ect_ctx* c, int config, const double2* rhs, double2* x, int k, const ect_options& opt,
+                 ect_stats* stats, bool same_rhs) {
+    ECT_REQUIRE(config == ECT_VACUUM || config == ECT_DEFECT, ECT_ERR_ARG, "config must be ECT_VACUUM or ECT_DEFECT");
+    const int F = (int)c->sweep_omega.size();
+    ECT_REQUIRE(F >= 1, ECT_ERR_STATE, "no frequency sweep assembled (ect_assemble_sweep)");
+    ECT_REQUIRE(k >= 1 && (int64_t)k * F <= 4096, ECT_ERR_ARG, "k per frequency must be >= 1 and k * F <= 4096");
+    Groups G;
+    for (int f = 0; f < F; ++f) G.push_back(Group{2 + 2 * f + config, f * k, k, same_rhs ? 0 : f * k});
+    solve_groups(c, G, rhs, x, k * F, opt, stats);
 }
 
 void cgs2_entry(ect_ctx* c, int precision, const void* V, int j, int64_t n, void* w, double* h, double* beta) {

@@ -149,16 +149,29 @@ void defect_coefficients(const std::vector<double>& s0, const std::vector<double
     }
 }
 
+}  // namespace
+
 // coefficients, conducting nodes and constraint mask of configuration m
 void upload_config(ect_ctx* c, int m, const std::vector<double>& s, const std::vector<double>& n) {
     const int64_t N = c->n_nodes, T = c->n_tets;
     Matrix& M = c->mat[m];
+    if (&M.h_sigma != &s) M.h_sigma = s;
+    if (&M.h_nu != &n) M.h_nu = n;
+    const bool plate = M.ibc && (int64_t)M.h_void.size() == T;
+    // conducting nodes and (with a plate removed by the IBC) nodes that keep a volume form
     M.h_cond.assign(N, 0);
-    for (int64_t t = 0; t < T; ++t)
-        if (s[t] > 0.0)
-            for (int a = 0; a < 4; ++a) M.h_cond[c->h_tets[4 * t + a]] = 1;
+    std::vector<uint8_t> live(N, plate ? 0 : 1);
+    for (int64_t t = 0; t < T; ++t) {
+        if (plate && M.h_void[t]) continue;
+        for (int a = 0; a < 4; ++a) {
+            live[c->h_tets[4 * t + a]] = 1;
+            if (s[t] > 0.0) M.h_cond[c->h_tets[4 * t + a]] = 1;
+        }
+    }
     std::vector<uint8_t> fm(N);
-    for (int64_t i = 0; i < N; ++i) fm[i] = (uint8_t)((c->h_bc[i] & 7) | (M.h_cond[i] ? 0 : 8));
+    for (int64_t i = 0; i < N; ++i)
+        fm[i] = live[i] ? (uint8_t)((c->h_bc[i] & 7) | (M.h_cond[i] ? 0 : 8)) : (uint8_t)15;  // plate inside: all fixed
+    M.h_fix = fm;
     cudaStream_t st = c->stream;
     M.sigma.alloc(sizeof(double) * T);
     M.nu.alloc(sizeof(double) * T);
@@ -169,6 +182,8 @@ void upload_config(ect_ctx* c, int m, const std::vector<double>& s, const std::v
     ECT_CUDA(cudaStreamSynchronize(st));
     M.assembled = M.pc_f64 = M.pc_f32 = false;
 }
+
+namespace {
 
 // Omega_d: the tets whose coefficients differ between the two configurations
 void upload_defect_list(ect_ctx* c, const std::vector<double>& s1, const std::vector<double>& n1) {
@@ -185,11 +200,17 @@ void upload_defect_list(ect_ctx* c, const std::vector<double>& s1, const std::ve
 
 }  // namespace
 
+void clear_sweep(ect_ctx* c) {
+    workspace_free(c);
+    c->smat.clear();
+    c->sweep_omega.clear();
+}
+
 void set_defect(ect_ctx* c, const double* sigma_d, const double* nu_d) {
     ECT_REQUIRE(c->mesh_set, ECT_ERR_STATE, "ect_set_mesh must come first");
     std::vector<double> s1, n1;
     defect_coefficients(c->h_sigma0, c->h_nu0, sigma_d, nu_d, s1, n1);
-    workspace_free(c);
+    clear_sweep(c);
     c->mat[1].reset();
     upload_config(c, 1, s1, n1);
     upload_defect_list(c, s1, n1);
@@ -233,8 +254,9 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
 
     // reset state
     c->mesh_set = false;
+    clear_sweep(c);
     for (int m = 0; m < 2; ++m) c->mat[m].reset();
-    workspace_free(c);
+    c->fine_plan.reset();
     c->n_nodes = n_nodes;
     c->n_tets = n_tets;
     c->n_blocks = (int64_t)bptr.size() - 1;

@@ -233,7 +233,9 @@ struct MgLevel {
     DevBuf agg_ptr_own, pinv_off_own, pinv32_off_own, pinv64_own, pinv32_own;
     DevBuf node_agg, clo, chi, w64, w32;
     DevBuf ap_ptr, ap_col, ap_val64, ap_val32;  // AP = A P (this level's rows, next level's columns)
+    std::vector<int32_t> h_ap_ptr, h_ap_col;
     bool has_ap = false;
+    StagedPlan plan, ap_plan;                // staged FP32 SpMM tilings of A (levels > 0) and AP
     DevBuf r, z, t;                          // cycle vectors (k right-hand sides)
 };
 
@@ -243,6 +245,8 @@ struct Multigrid {
     DevBuf einv64, einv32, rc, zc, gpart;
     int64_t kcap = 0;
     bool f32 = false;
+    const StagedPlan* fine_plan = nullptr;   // the context's plan of the finest pattern
+    int staged_rows = -1;                    // rows per staged tile the level plans were built for
 };
 
 void mg_free(Matrix& M) {
@@ -343,6 +347,8 @@ void build_ap(cudaStream_t st, MgLevel& L, const std::vector<int32_t>& nagg, boo
     DevBuf d_sptr, d_src;
     to_device(L.ap_ptr, ptr, st);
     to_device(L.ap_col, col, st);
+    L.h_ap_ptr = ptr;
+    L.h_ap_col = col;
     to_device(d_sptr, sptr, st);
     to_device(d_src, src, st);
     L.ap_val64.alloc(sizeof(double2) * 16 * std::max<int64_t>(nnz, 1));
@@ -387,7 +393,7 @@ void ap_update(cudaStream_t st, const MgLevel& L, const C<T>* e, int64_t lde, C<
 }  // namespace
 
 void mg_setup(ect_ctx* c, int which, bool f32) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     mg_free(M);
     cudaStream_t st = c->stream;
     Multigrid* G = new Multigrid();
@@ -416,7 +422,7 @@ void mg_setup(ect_ctx* c, int which, bool f32) {
         L.h_free.resize(4 * L.n);
         for (int64_t i = 0; i < L.n; ++i)
             for (int p = 0; p < 4; ++p)
-                L.h_free[4 * i + p] = p < 3 ? !((c->h_bc[i] >> p) & 1) : (M.h_cond[i] != 0);
+                L.h_free[4 * i + p] = !((M.h_fix[i] >> p) & 1);
         L.w64.alloc(sizeof(double) * 4 * L.n);
         k_finest_weights<<<grid_for(4 * L.n, 256), 256, 0, st>>>(M.t.as<double>(), M.fixmask.as<uint8_t>(), L.n,
                                                                  L.w64.as<double>());
@@ -626,8 +632,13 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
     const int gamma = last ? 1 : 2;
     // t = r - A z: one thread per scalar row, or one warp per block row on the small coarse
     // levels (few rows, many blocks per row: the warp splits the row's serial chain of loads)
+    const StagedPlan* plan = l == 0 ? G->fine_plan : &L.plan;
+    const bool staged = std::is_same<T, float>::value && G->staged_rows > 0 && plan && plan->ok;
     auto residual = [&]() {
-        if (L.n <= WARP_ROW_MAX_NODES)
+        if (staged && L.n > WARP_ROW_MAX_NODES)
+            bsr_spmm_staged_f32(st, *plan, L.rp, (const float2*)val, (const float2*)z, ld, (const float2*)r,
+                                (float2*)t, ld, k, active);
+        else if (L.n <= WARP_ROW_MAX_NODES)
             bsr_spmv_warp<T>(st, L.rp, L.col, val, L.n, z, r, t, k, ld, tile, active);
         else if (std::is_same<T, double>::value)
             bsr_spmv_f64(st, L.rp, L.col, (const double2*)val, L.n, (const double2*)z, (const double2*)r, (double2*)t,
@@ -645,7 +656,13 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
         cycle<T>(st, G, l + 1, rn, zn, k, tile, active);
         k_prolong<T><<<dim3(grid_for(4 * L.n, 256), k), 256, 0, st>>>(z, ld, L.node_agg.as<int32_t>(), w, L.n, zn, ldn,
                                                                         active);
-        if (L.has_ap) ap_update<T>(st, L, zn, ldn, t, ld, k, tile, active);
+        if (L.has_ap) {
+            if (std::is_same<T, float>::value && G->staged_rows > 0 && L.ap_plan.ok)
+                bsr_spmm_staged_f32(st, L.ap_plan, L.ap_ptr.as<int32_t>(), L.ap_val32.as<float2>(),
+                                    (const float2*)zn, ldn, (const float2*)t, (float2*)t, ld, k, active);
+            else
+                ap_update<T>(st, L, zn, ldn, t, ld, k, tile, active);
+        }
     }
     if (!L.has_ap) residual();
     block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, t, z, k, ld, tile, active, true);
@@ -655,17 +672,49 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
 }  // namespace
 
 void mg_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld, int tile, const int* active) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.mg && M.mg->kcap >= k, ECT_ERR_STATE, "multigrid scratch not ready (internal)");
     ECT_REQUIRE(ld == 4 * c->n_nodes, ECT_ERR_ARG, "multigrid vectors must be packed");
     cycle<double>(c->stream, M.mg, 0, r, z, k, tile, active);
 }
 
 void mg_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld, int tile, const int* active) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.mg && M.mg->kcap >= k && M.mg->f32, ECT_ERR_STATE, "FP32 multigrid not ready");
     ECT_REQUIRE(ld == 4 * c->n_nodes, ECT_ERR_ARG, "multigrid vectors must be packed");
     cycle<float>(c->stream, M.mg, 0, r, z, k, tile, active);
+}
+
+void staged_prepare(ect_ctx* c, int which) {
+    const int rows = c->staged_rows;
+    Multigrid* G = ctx_mat(c, which).mg;
+    if (rows <= 0) {
+        if (G) G->staged_rows = -1;
+        return;
+    }
+    cudaStream_t st = c->stream;
+    if (c->fine_plan.rows != rows) {
+        staged_plan_build(st, c->fine_plan, c->h_row_ptr, c->h_col, c->n_nodes, c->n_nodes, rows);
+        ++c->plan_gen;
+    }
+    if (!G) return;
+    G->fine_plan = &c->fine_plan;
+    if (G->f32) {
+        bool rebuilt = false;
+        for (size_t l = 0; l < G->L.size(); ++l) {
+            MgLevel& L = G->L[l];
+            if (l > 0 && L.n > WARP_ROW_MAX_NODES && L.plan.rows != rows) {
+                staged_plan_build(st, L.plan, L.h_rp, L.h_col, L.n, L.n, rows);
+                rebuilt = true;
+            }
+            if (L.has_ap && L.ap_plan.rows != rows) {
+                staged_plan_build(st, L.ap_plan, L.h_ap_ptr, L.h_ap_col, L.n, L.n_next, rows);
+                rebuilt = true;
+            }
+        }
+        if (rebuilt) ++c->plan_gen;
+    }
+    G->staged_rows = rows;
 }
 
 int mg_levels(const Matrix& M) { return M.mg ? (int)M.mg->L.size() + 1 : 0; }

@@ -459,7 +459,7 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
 // between the groups' conducting nodes (assembled on the host in a fixed
 // order), inverted on the device.
 void coarse_setup(ect_ctx* c, int which, int group) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     cudaStream_t st = c->stream;
     const int64_t N = c->n_nodes, nb = c->n_blocks;
     M.nc = 0;
@@ -638,8 +638,8 @@ template void dense_gemv<float>(cudaStream_t, const float2*, int64_t, const floa
                                 float2*);
 
 void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) {
-    ECT_REQUIRE(which == ECT_VACUUM || which == ECT_DEFECT, ECT_ERR_ARG, "bad which");
-    Matrix& M = c->mat[which];
+    ECT_REQUIRE(which_valid(c, which), ECT_ERR_ARG, "bad which");
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "ect_assemble must come before ect_precond_setup");
     bool f32 = (precision_mask & ECT_F32) != 0;
     cudaStream_t st = c->stream;
@@ -675,7 +675,7 @@ void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) 
 }
 
 void coarse_scratch(ect_ctx* c, int which, int k) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     if (M.mg && !mg_ready(M, k)) {  // new cycle vectors: captured graphs hold the old ones
         workspace_free(c);
         mg_scratch(M, k);
@@ -690,7 +690,7 @@ void coarse_scratch(ect_ctx* c, int which, int k) {
 
 void precond_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int k, int64_t ld, int rhs_tile,
                        const int* active) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.pc_f64, ECT_ERR_STATE, "preconditioner not set up");
     if (M.mg) {
         mg_apply_f64(c, which, r, z, k, ld, rhs_tile, active);
@@ -702,7 +702,7 @@ void precond_apply_f64(ect_ctx* c, int which, const double2* r, double2* z, int 
 
 void precond_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int64_t ld, int rhs_tile,
                        const int* active) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.pc_f32, ECT_ERR_STATE, "FP32 preconditioner not set up (use ECT_F32 in ect_precond_setup)");
     if (M.mg) {
         mg_apply_f32(c, which, r, z, k, ld, rhs_tile, active);

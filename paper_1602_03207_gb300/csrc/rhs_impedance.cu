@@ -283,10 +283,22 @@ void coil_rhs(ect_ctx* c, const ect_coil& coil, const double* h_z, int k, double
 
 // u0, ud, b: [n_pos][2][4N]; h_dz (and h_dz_emf): [n_pos][2][2] complex
 void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b, const double* cur, int n_pos,
-             double* h_dz, double* h_dz_emf) {
+             double* h_dz, double* h_dz_emf, double omega) {
+    if (omega <= 0.0) omega = c->omega;
     ECT_REQUIRE(c->mesh_set && c->physics_set, ECT_ERR_STATE, "mesh and physics must be set");
     ECT_REQUIRE(u0 && ud && cur && h_dz && n_pos >= 1, ECT_ERR_ARG, "bad delta_z arguments");
     ECT_REQUIRE(cur[0] != 0.0 && cur[1] != 0.0, ECT_ERR_ARG, "coil currents must be non-zero");
+    ECT_REQUIRE(!h_dz_emf || b, ECT_ERR_ARG, "h_dz_emf needs d_b");
+    // With the impedance boundary condition the plate's volume fields are not computed, so
+    // the volume form of Eq. impedkl has nothing to integrate: Delta Z is the coil-EMF
+    // difference, which needs the sources.
+    const bool emf_only = c->mat[0].ibc || c->mat[1].ibc;
+    ECT_REQUIRE(!emf_only || b, ECT_ERR_ARG, "with the impedance boundary condition Delta Z needs d_b (EMF form)");
+    std::vector<double> emf_tmp;
+    if (emf_only && !h_dz_emf) {
+        emf_tmp.resize(8 * (size_t)n_pos);
+        h_dz_emf = emf_tmp.data();
+    }
     cudaStream_t st = c->stream;
     const int64_t nvec = 4 * c->n_nodes;
     int G = (int)std::min<int64_t>(std::max<int64_t>(1, (c->n_omega_d + DZ_TPB - 1) / DZ_TPB), 304);
@@ -297,7 +309,7 @@ void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b,
     k_delta_z<<<dim3(G, n_pos), DZ_TPB, 0, st>>>(c->omega_d.as<int32_t>(), c->n_omega_d, c->tets.as<int32_t>(),
                                                  c->geo.as<double>(), c->mat[0].sigma.as<double>(),
                                                  c->mat[0].nu.as<double>(), c->mat[1].sigma.as<double>(),
-                                                 c->mat[1].nu.as<double>(), c->omega, c->delta, u0, ud, nvec,
+                                                 c->mat[1].nu.as<double>(), omega, c->delta, u0, ud, nvec,
                                                  part.as<double>());
     ECT_CHECK_LAUNCH();
     if (h_dz_emf && b) {
@@ -308,7 +320,7 @@ void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b,
     ECT_CUDA(cudaMemcpyAsync(hp.data(), part.p, part.bytes, cudaMemcpyDeviceToHost, st));
     if (h_dz_emf && b) ECT_CUDA(cudaMemcpyAsync(he.data(), parte.p, parte.bytes, cudaMemcpyDeviceToHost, st));
     ECT_CUDA(cudaStreamSynchronize(st));
-    const double om = c->omega;
+    const double om = omega;
     for (int p = 0; p < n_pos; ++p) {
         for (int kl = 0; kl < 4; ++kl) {
             const int kk = kl >> 1, l = kl & 1;
@@ -333,6 +345,8 @@ void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b,
             }
         }
     }
+    if (emf_only)
+        for (int64_t e = 0; e < 8 * (int64_t)n_pos; ++e) h_dz[e] = h_dz_emf[e];
 }
 
 // ----------------------------------------------------------------------------
@@ -389,7 +403,7 @@ double* dz_static_scratch() {
 extern "C" int ect_delta_z_static(ect_ctx* c, const void* d_u0, const void* d_ud, const void* d_b,
                                   const double* h_current, int n_pos, double* h_dz, double* h_dz_emf) {
     if (!c) return ECT_ERR_ARG;
-    try {
+    return guarded_call(c, [&] {
         ECT_REQUIRE(c->mesh_set && c->physics_set, ECT_ERR_STATE, "mesh and physics must be set");
         ECT_REQUIRE(d_u0 && d_ud && h_current && h_dz, ECT_ERR_ARG, "null argument");
         ECT_REQUIRE(n_pos >= 1, ECT_ERR_ARG, "n_pos must be >= 1");
@@ -397,6 +411,8 @@ extern "C" int ect_delta_z_static(ect_ctx* c, const void* d_u0, const void* d_ud
                     "ect_delta_z_static handles at most 64 positions per call (its static scratch size)");
         ECT_REQUIRE(!h_dz_emf || d_b, ECT_ERR_ARG, "h_dz_emf needs d_b");
         ECT_REQUIRE(h_current[0] != 0.0 && h_current[1] != 0.0, ECT_ERR_ARG, "coil currents must be non-zero");
+        ECT_REQUIRE(!c->mat[0].ibc && !c->mat[1].ibc, ECT_ERR_STATE,
+                    "with the impedance boundary condition use ect_delta_z (EMF form)");
         double* base = dz_static_scratch();
         double* part = base;                                              // [n_pos][G][8]
         double* parte = base + (int64_t)DZ_STATIC_MAX_POS * DZ_STATIC_G * 8;  // [n_pos][Ge][8]
@@ -439,13 +455,5 @@ extern "C" int ect_delta_z_static(ect_ctx* c, const void* d_u0, const void* d_ud
                     e[1] = -f * er;
                 }
             }
-        c->err.clear();
-        return ECT_OK;
-    } catch (const EctError& e) {
-        c->err = e.msg;
-        return e.code;
-    } catch (...) {
-        c->err = "unknown error";
-        return ECT_ERR_ARG;
-    }
+    });
 }

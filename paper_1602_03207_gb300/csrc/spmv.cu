@@ -348,7 +348,7 @@ void bsr_spmv_f32(cudaStream_t st, const int32_t* rp, const int32_t* cl, const f
 
 void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, int k, int64_t ldx, int rhs_tile,
               const int* active) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "matrix not assembled");
     const double2* val = scaled ? M.sval.as<double2>() : M.val.as<double2>();
     bsr_spmv_f64(c->stream, c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), val, c->n_nodes, x, nullptr, y, k, ldx,
@@ -357,8 +357,13 @@ void spmv_f64(ect_ctx* c, int which, bool scaled, const double2* x, double2* y, 
 
 void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t ldx, int rhs_tile,
               const int* active) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.assembled && M.has_f32, ECT_ERR_STATE, "FP32 matrix not assembled (use ECT_F32 in ect_assemble)");
+    if (c->staged_rows > 0 && rhs_tile != -1 && c->fine_plan.ok && c->fine_plan.rows == c->staged_rows) {
+        bsr_spmm_staged_f32(c->stream, c->fine_plan, c->row_ptr.as<int32_t>(), M.sval32.as<float2>(), x, ldx,
+                            nullptr, y, ldx, k, active);
+        return;
+    }
     bsr_spmv_f32(c->stream, c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), M.sval32.as<float2>(), c->n_nodes, x,
                  nullptr, y, k, ldx, rhs_tile, active);
 }
@@ -389,7 +394,7 @@ template void bsr_spmv_warp<float>(cudaStream_t, const int32_t*, const int32_t*,
 
 void spmv_df32(ect_ctx* c, int which, const float2* u, double2* y, int k, int64_t ldx, int rhs_tile,
                const int* active) {
-    Matrix& M = c->mat[which];
+    Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.assembled && M.has_f32, ECT_ERR_STATE, "FP32 matrix not assembled (use ECT_F32 in ect_assemble)");
     const int32_t* rp = c->row_ptr.as<int32_t>();
     const int32_t* cl = c->col.as<int32_t>();

@@ -26,6 +26,11 @@ ECT_VACUUM, ECT_DEFECT = 0, 1
 ECT_F64, ECT_F32 = 1, 2
 ECT_MODE_F64, ECT_MODE_MIXED = 0, 1
 
+
+def sweep_matrix(f, config):
+    """Matrix index of configuration `config` at sweep frequency f (ECT_SWEEP_MATRIX)."""
+    return 2 + 2 * int(f) + int(config)
+
 _NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_CUDA", 4: "ERR_OOM", 5: "ERR_NOT_CONVERGED",
           6: "ERR_BREAKDOWN", 7: "ERR_TIMEOUT", 8: "ERR_STATE"}
 
@@ -33,7 +38,8 @@ _NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_CUDA", 4: "ERR_OOM", 5: 
 EXPORTS = ["ect_default_options", "ect_create", "ect_destroy", "ect_last_error", "ect_set_mesh",
            "ect_set_physics", "ect_assemble", "ect_precond_setup", "ect_matrix_info", "ect_matrix_copy",
            "ect_scaling_copy", "ect_spmv", "ect_precond_apply", "ect_cgs2", "ect_coil_rhs", "ect_solve",
-           "ect_delta_z", "ect_impedance", "ect_autotune", "ect_set_defect", "ect_delta_z_static", "ect_mlp_num_params", "ect_mlp_create",
+           "ect_delta_z", "ect_impedance", "ect_autotune", "ect_set_defect", "ect_delta_z_static", "ect_set_spmm_rows", "ect_partition", "ect_set_ibc", "ect_assemble_sweep", "ect_solve_sweep",
+           "ect_impedance_sweep", "ect_mlp_num_params", "ect_mlp_create",
            "ect_mlp_destroy", "ect_mlp_last_error", "ect_mlp_set_params", "ect_mlp_get_params", "ect_mlp_forward",
            "ect_mlp_gradients", "ect_mlp_train_step"]
 
@@ -53,7 +59,8 @@ class Coil(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("mode", ctypes.c_int), ("inner_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("rhs_tile", ctypes.c_int), ("timeout_s", ctypes.c_double), ("reorth", ctypes.c_int)]
+                ("rhs_tile", ctypes.c_int), ("timeout_s", ctypes.c_double), ("reorth", ctypes.c_int),
+                ("spmm_rows", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -93,6 +100,12 @@ def load_library(path=LIB_PATH):
         "ect_scaling_copy": (I, [P, I, P]),
         "ect_spmv": (I, [P, I, I, P, P, I]),
         "ect_precond_apply": (I, [P, I, I, P, P, I]),
+        "ect_set_spmm_rows": (I, [P, I]),
+        "ect_partition": (I, [P, I64, I, P, P]),
+        "ect_set_ibc": (I, [P, I, P, D, D]),
+        "ect_assemble_sweep": (I, [P, P, I, I]),
+        "ect_solve_sweep": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
+        "ect_impedance_sweep": (I, [P, ctypes.POINTER(Coil), P, I, ctypes.POINTER(Options), P, ctypes.POINTER(Stats)]),
         "ect_cgs2": (I, [P, I, P, I, I64, P, P, P]),
         "ect_coil_rhs": (I, [P, ctypes.POINTER(Coil), P, I, P]),
         "ect_solve": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
@@ -128,6 +141,19 @@ def default_options(**kw):
     return o
 
 
+def partition(xyz, max_block_nodes=16):
+    """Recursive coordinate bisection (ect_partition): returns (new_id, block_of_new)."""
+    L = load_library()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    new_id = np.empty(n, dtype=np.int32)
+    blk = np.empty(n, dtype=np.int32)
+    rc = L.ect_partition(_ptr(xyz), n, int(max_block_nodes), _ptr(new_id), _ptr(blk))
+    if rc != 0:
+        raise EctError(rc, L.ect_last_error(None).decode())
+    return new_id, blk
+
+
 def _ptr(a):
     """Host pointer of a contiguous numpy array (None -> NULL)."""
     if a is None:
@@ -161,6 +187,7 @@ class Context:
             raise EctError(rc, self.L.ect_last_error(None).decode())
         self.h = h
         self.n_nodes = 0
+        self.n_sweep = 0
 
     def close(self):
         if getattr(self, "h", None):
@@ -208,6 +235,11 @@ class Context:
         nd = None if nu_d is None else np.ascontiguousarray(nu_d, dtype=np.float64)
         self._call(self.L.ect_set_defect, _ptr(sd), _ptr(nd))
 
+    def set_ibc(self, which, plate, sigma_p, nu_p):
+        """Impedance boundary condition on the surface of the tets flagged in `plate` (None clears)."""
+        arr = None if plate is None else np.ascontiguousarray(plate, dtype=np.uint8)
+        self._call(self.L.ect_set_ibc, int(which), None if arr is None else _ptr(arr), float(sigma_p), float(nu_p))
+
     def set_physics(self, freq_hz, nu_tilde, delta_gauge):
         self._call(self.L.ect_set_physics, float(freq_hz), float(nu_tilde), float(delta_gauge))
 
@@ -247,6 +279,9 @@ class Context:
     # ---- kernels -------------------------------------------------------------
     def spmv(self, which, x, y, k=1, precision=ECT_F64):
         self._call(self.L.ect_spmv, int(which), int(precision), _dptr(x), _dptr(y), int(k))
+
+    def set_spmm_rows(self, rows):
+        self._call(self.L.ect_set_spmm_rows, int(rows))
 
     def precond_apply(self, which, r, z, k=1, precision=ECT_F64):
         self._call(self.L.ect_precond_apply, int(which), int(precision), _dptr(r), _dptr(z), int(k))
@@ -315,6 +350,33 @@ class Context:
         except EctError as e:
             e.stats = st.as_dict()
             raise
+        return dz[..., 0] + 1j * dz[..., 1], st.as_dict()
+
+
+    def assemble_sweep(self, freqs_hz, precision_mask=ECT_F64):
+        f = np.ascontiguousarray(np.atleast_1d(freqs_hz), dtype=np.float64)
+        self._call(self.L.ect_assemble_sweep, _ptr(f), int(f.size), int(precision_mask))
+        self.n_sweep = int(f.size)
+
+    def solve_sweep(self, config, rhs, x, k, options=None):
+        o = options if options is not None else default_options()
+        st = Stats()
+        try:
+            self._call(self.L.ect_solve_sweep, int(config), _dptr(rhs), _dptr(x), int(k), ctypes.byref(o),
+                       ctypes.byref(st), stats=st)
+        except EctError as e:
+            e.stats = st.as_dict()
+            raise
+        return st.as_dict()
+
+    def impedance_sweep(self, coils, z_pos, options=None):
+        z = np.ascontiguousarray(np.atleast_1d(z_pos), dtype=np.float64)
+        arr = (Coil * 2)(coil(coils[0]), coil(coils[1]))
+        o = options if options is not None else default_options()
+        dz = np.empty((self.n_sweep, z.size, 2, 2, 2), dtype=np.float64)
+        st = Stats()
+        self._call(self.L.ect_impedance_sweep, arr, _ptr(z), int(z.size), ctypes.byref(o), _ptr(dz),
+                   ctypes.byref(st), stats=st)
         return dz[..., 0] + 1j * dz[..., 1], st.as_dict()
 
 

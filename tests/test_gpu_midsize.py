@@ -1,0 +1,76 @@
+"""Delta Z against the oracle at scale (the benchmark spec's 1e-6 bar beyond the
+8k-node parity configuration).
+
+Expected values come from tests/golden/make_golden.py (CPU oracle only):
+  * tsp_mid: a 53 x 53 x 120-node jittered support-plate mesh (337,080 nodes,
+    1,348,320 complex unknowns), probe at the plate edge, every system solved
+    by the oracle's FGMRES with its own aggregation multigrid to a relative
+    residual of 1e-11; its reciprocity and EMF forms agree to 4e-12;
+  * c5_deposit: config 5's 50 x 50 x 100 mesh (250,000 nodes) with the
+    deposit of seed 0, two probe positions, same oracle.
+The GPU solves every system in FP64 and in mixed precision to 1e-10 and
+Delta Z must match the oracle's elementwise over the 2 x 2 matrix to 1e-6 of
+its largest entry."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import ect_inputs as E
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden(name):
+    path = os.path.join(HERE, "golden", name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not written (python tests/golden/make_golden.py)")
+    return json.load(open(path))
+
+
+def _cm(a):
+    return np.array([[complex(*v) for v in row] for row in a])
+
+
+def _run(p, zs, ref):
+    from paper_1602_03207_gb300 import build, ect
+    build.build()
+    ect.load_library()
+    ctx = ect.Context()
+    ctx.load_problem(p)
+    mask = ect.ECT_F64 | ect.ECT_F32
+    for w in (ect.ECT_VACUUM, ect.ECT_DEFECT):
+        ctx.assemble(w, mask)
+        ctx.precond_setup(w, mask, -1)
+    out = {}
+    for mode in ("mixed", "f64"):
+        opts = ect.default_options(tol=1e-10, mode=ect.ECT_MODE_MIXED if mode == "mixed" else ect.ECT_MODE_F64,
+                                   restart=16 if mode == "mixed" else 30, inner_iters=20, max_iters=400 if
+                                   mode == "mixed" else 6000)
+        dz, st = ctx.impedance(p.coils, np.asarray(zs), opts)
+        for q, r in enumerate(ref):
+            err = np.abs(dz[q] - r).max() / np.abs(r).max()
+            out[(mode, q)] = err
+            assert err <= 1e-6, (mode, q, err, st)
+    ctx.close()
+    return out
+
+
+def test_delta_z_midsize_support_plate_against_oracle():
+    g = _golden("tsp_mid_oracle.json")
+    p = E.tsp_problem((53, 53, 120), (30e-3, 30e-3, 67.4e-3), (2, 2, 4), 0.15, 0, z_pos=(10e-3,))
+    assert p.mesh.n_nodes == g["n_nodes"]
+    ref = [_cm(pos["dz"]) for pos in g["positions"]]
+    _run(p, [pos["z"] for pos in g["positions"]], ref)
+
+
+def test_delta_z_config5_deposit_against_oracle():
+    g = _golden("c5_deposit_oracle.json")
+    shape, lengths, _ = E.CONFIGS["c5"]
+    p = E.deposit_problem(shape, lengths, np.array(g["params"]), z_pos=[pos["z"] for pos in g["positions"]])
+    assert p.mesh.n_nodes == g["n_nodes"]
+    ref = [_cm(pos["dz"]) for pos in g["positions"]]
+    _run(p, [pos["z"] for pos in g["positions"]], ref)

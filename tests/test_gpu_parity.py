@@ -1,7 +1,7 @@
 """GPU parity: every step of the CUDA path against the FP64 CPU oracle.
 
 All GPU work goes through the C ABI (libect.so via the ctypes binding).
-Tolerances (derived in the design notes):
+Tolerances (derived from the arithmetic of each step):
   assembly / FP64 SpMV   |diff_ij| <= 1e-12 sqrt(|M_ii| |M_jj|)   (sum of ~24
                           tet terms, each ~10 roundings of 1.1e-16)
   FP32 scaled SpMV       <= 2e-6 relative (unit-scaled entries, 15 blocks/row)
@@ -132,19 +132,47 @@ def test_spmv_f64_batch(ect, small):
         assert np.abs(Y - ref).max() <= 1e-13 * scale, k
 
 
-def test_spmv_f32_scaled(ect, small):
+@pytest.mark.parametrize("rows", [0, 8, 64, -1])          # staged tilings (auto = 32) and the unstaged kernel
+def test_spmv_f32_scaled(ect, small, rows):
     p, ctx, M = small
     rng = np.random.default_rng(1)
     n = 4 * p.mesh.n_nodes
     t = fem.scaling(M["vacuum"])
     S = fem.scaled(M["vacuum"], t)
-    X = crand(rng, 2, n)
-    x = dev(X, torch.complex64)
-    y = torch.empty_like(x)
-    ctx.spmv(WHICH["vacuum"], x, y, 2, precision=ect.ECT_F32)
-    ref = (S @ X.T).T
-    err = np.linalg.norm(y.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
-    assert err.max() <= 2e-6
+    ctx.set_spmm_rows(rows)
+    for k in (1, 2, 8, 11, 19):                             # full and partial right-hand-side tiles
+        X = crand(rng, k, n)
+        x = dev(X, torch.complex64)
+        y = torch.empty_like(x)
+        ctx.spmv(WHICH["vacuum"], x, y, k, precision=ect.ECT_F32)
+        ref = (S @ X.T).T
+        err = np.linalg.norm(y.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() <= 2e-6, (rows, k)
+    ctx.set_spmm_rows(0)
+
+
+def test_spmv_f32_staged_many_tiles(ect):
+    """Staged SpMM on a mesh of ~1000 tiles of 16 rows (ragged last tile, 14-15
+    blocks per row), elementwise against the oracle's scaled matrix."""
+    p = E.wall_loss_problem((27, 25, 26), (20e-3, 20e-3, 30e-3), (2, 2, 4), 0.15, 3, z_pos=(0.0,))
+    ctx = ect.Context()
+    ctx.load_problem(p)
+    ctx.assemble(ect.ECT_DEFECT, ect.ECT_F64 | ect.ECT_F32)
+    S = fem.scaled(fem.system_matrix(p, "defect"), ctx.scaling_copy(ect.ECT_DEFECT))
+    rng = np.random.default_rng(7)
+    X = crand(rng, 9, S.shape[0]).astype(np.complex64)
+    ref = (S @ X.T.astype(np.complex128)).T
+    for rows in (16, 0):
+        ctx.set_spmm_rows(rows)
+        x = dev(X, torch.complex64)
+        y = torch.empty_like(x)
+        ctx.spmv(ect.ECT_DEFECT, x, y, 9, precision=ect.ECT_F32)
+        Y = y.cpu().numpy()
+        scale = np.abs(S).max() * np.abs(X).max()
+        assert np.abs(Y - ref).max() <= 1e-5 * scale, rows
+        err = np.linalg.norm(Y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() <= 2e-6, rows
+    ctx.close()
 
 
 def _oracle_amg(p, M, which):
@@ -159,32 +187,44 @@ def _oracle_amg(p, M, which):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("shape", [(10, 11, 13), (17, 16, 21)])
+@pytest.mark.parametrize("shape", [(10, 11, 13), (17, 16, 21), (30, 30, 24)])
 def test_multigrid_apply_matches_oracle(ect, prec, shape):
     """One W-cycle (2 and 3 levels) against the oracle's, same hierarchy rules.
 
-    The cycle's output is dominated by the coarsest-level correction of the
-    near-null (gauge) modes, eigenvalues ~1e-6 of the scaled operator, so
-    rounding differences are amplified by ~1e6: FP64 agrees to ~1e-8, FP32
-    (eps 6e-8) to 1e-3..1e-2 depending on the summation order of each level's
-    kernels.  The solve tests gate the final accuracy on the true residual."""
+    Metric e_S = ||S (z - z_ref)|| / ||S z_ref|| per right-hand side (S the
+    scaled finest matrix): z is dominated by the coarse correction of the
+    near-null gauge modes, which S damps, so e_S sees errors on every level
+    (pinned in test_oracle_multigrid_metric: an FP32 execution of the
+    oracle's cycle stays below a tenth of the FP32 bound, indexing errors
+    planted on a coarse level exceed it).  Bounds: FP32 1e-2 (the GPU's FP32
+    cycles measured <= 3.9e-3, median ~2e-3, here); FP64
+    1e-7: the GPU inverts the coarsest operator (condition ~1e8) by Gauss-Jordan,
+    the oracle by LAPACK, so the two coarse corrections differ by ~kappa eps64
+    ~1e-8 relative (measured 2-3e-9 in e_S).  The 30 x 30 x 24 mesh (21,600 nodes) has the residual updates
+    t -= AP e and the shared-memory-staged SpMM on its finest level; it runs
+    the FP32 cycle with the staged kernels and with the unstaged ones."""
     p = E.wall_loss_problem(shape, (20e-3, 20e-3, 30e-3), (2, 2, 2), 0.15, 4, z_pos=(0.0,))
     ctx = make_ctx(ect, p, group=-1)
     M = fem.system_matrix(p, "defect")
     lv = _oracle_amg(p, M, "defect")
+    S = fem.scaled(M, fem.scaling(M))
     assert len(lv) >= (3 if shape[0] > 10 else 2)
     rng = np.random.default_rng(11)
     n = 4 * p.mesh.n_nodes
-    k = 19                                       # two full tiles of 8, then 2 and 1
+    k = 19 if shape[0] < 30 else 11              # full tiles of 8, then partial ones
     R = crand(rng, k, n)
-    dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-7) if prec == "f64" else (torch.complex64, ect.ECT_F32, 3e-2))
-    r = dev(R, dt)
-    z = torch.empty_like(r)
-    ctx.precond_apply(1, r, z, k, precision=pr)
-    Z = z.cpu().numpy()
     refs = [solve.amg_apply(lv, R[q]) for q in range(k)]
-    errs = [np.linalg.norm(Z[q] - refs[q]) / np.linalg.norm(refs[q]) for q in range(k)]
-    assert max(errs) <= tol, (int(np.argmax(errs)), max(errs), float(np.median(errs)))
+    dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-7) if prec == "f64" else (torch.complex64, ect.ECT_F32, 1e-2))
+    r = dev(R, dt)
+    for rows in ((0, -1) if prec == "f32" else (0,)):
+        ctx.set_spmm_rows(rows)
+        z = torch.empty_like(r)
+        ctx.precond_apply(1, r, z, k, precision=pr)
+        Z = z.cpu().numpy()
+        es = [np.linalg.norm(S @ (Z[q] - refs[q])) / np.linalg.norm(S @ refs[q]) for q in range(k)]
+        assert max(es) <= tol, (rows, int(np.argmax(es)), max(es), float(np.median(es)))
+    ctx.set_spmm_rows(0)
+    ctx.close()
 
 
 @pytest.mark.parametrize("mode", ["f64", "mixed"])
@@ -279,6 +319,16 @@ def test_solve_residual_with_oracle_matrix(ect, small, mode, graph):
     p, ctx, M = small
     opts = ect.default_options(tol=1e-10, restart=30, use_graph=graph,
                                mode=ect.ECT_MODE_F64 if mode == "f64" else ect.ECT_MODE_MIXED, inner_iters=20)
+    for w in WHICH:
+        X, st = _solve_check(ect, p, ctx, M, w, opts)
+        assert st["converged"] == 2
+
+
+@pytest.mark.parametrize("rows", [8, 16, -1])
+def test_mixed_solve_spmm_tilings(ect, small, rows):
+    """Mixed mode with the staged FP32 SpMM at other row tilings and with the unstaged kernels."""
+    p, ctx, M = small
+    opts = ect.default_options(tol=1e-10, restart=16, mode=ect.ECT_MODE_MIXED, inner_iters=16, spmm_rows=rows)
     for w in WHICH:
         X, st = _solve_check(ect, p, ctx, M, w, opts)
         assert st["converged"] == 2

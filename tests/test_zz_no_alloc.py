@@ -11,8 +11,24 @@ import pytest
 
 import ect_inputs as E
 
-pytestmark = pytest.mark.gpu
+import os
+import re
+
 torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_static_path_source_allocates_nothing():
+    """CPU check of the property that defines the entry point: the code from the
+    static scratch lookup to the end of ect_delta_z_static names no device
+    allocation (no DevBuf, alloc/ensure, cudaMalloc*, cudaFree*)."""
+    src = open(os.path.join(ROOT, "paper_1602_03207_gb300", "csrc", "rhs_impedance.cu")).read()
+    start = src.index("double* dz_static_scratch()")
+    body = src[start:]
+    assert "ect_delta_z_static" in body
+    code = re.sub(r"//[^\n]*", "", body)                       # comments may mention the words
+    for bad in ("DevBuf", ".alloc(", ".ensure(", "cudaMalloc", "cudaFree", "new ", "torch"):
+        assert bad not in code, bad
 
 
 @pytest.fixture(scope="module")
@@ -43,6 +59,7 @@ def case():
     return ect, ctx, B, U0, Ud, cur, P
 
 
+@pytest.mark.gpu
 def test_static_delta_z_matches_allocating_entry_point_twice(case):
     ect, ctx, B, U0, Ud, cur, P = case
     ref = [ctx.delta_z(U0[q], Ud[q], B[q], cur) for q in range(P)]
@@ -60,6 +77,7 @@ def test_static_delta_z_matches_allocating_entry_point_twice(case):
         assert np.abs(dz1[0] - ref[1][0]).max() <= 1e-12 * np.abs(ref[1][0]).max()
 
 
+@pytest.mark.gpu
 def test_static_delta_z_rejects_too_many_positions(case):
     ect, ctx, B, U0, Ud, cur, P = case
     with pytest.raises(ect.EctError) as e:

@@ -530,6 +530,7 @@ def kernel_probe(args):
     ctx.load_problem(p)
     ctx.assemble(0, ect.ECT_F64 | ect.ECT_F32)
     ctx.precond_setup(0, ect.ECT_F64 | ect.ECT_F32, -1 if args.probe_mg else 0)
+    ctx.set_spmm_rows(args.spmm_rows)
     n = 4 * p.mesh.n_nodes
     k = 8
     x = torch.randn(k, n, dtype=torch.complex64, device="cuda")
@@ -544,6 +545,41 @@ def kernel_probe(args):
     torch.cuda.synchronize()
     print(json.dumps({"kernel_probe": "ok", "dof": n, "nnzb": int(ctx.matrix_info()[1]),
                       "preconditioner": "multigrid" if args.probe_mg else "block-Jacobi"}))
+
+
+def dz_record(args):
+    """Delta Z of the mixed solve (to args.tol) against the plain FP64 solve (to 1e-10) at one
+    probe position of args.config, both through ect_impedance: the error record config 4 asks
+    for (mixed precision to 1e-8 at 16M unknowns)."""
+    import torch
+
+    import ect_inputs as E
+    from paper_1602_03207_gb300 import build as B
+    from paper_1602_03207_gb300 import ect
+
+    B.build()
+    p = E.make_config(args.config)
+    ctx = ect.Context()
+    ctx.load_problem(p)
+    for w in (0, 1):
+        ctx.assemble(w, ect.ECT_F64 | ect.ECT_F32)
+        ctx.precond_setup(w, ect.ECT_F64 | ect.ECT_F32, -1)
+    mixed = ect.default_options(tol=args.tol, mode=ect.ECT_MODE_MIXED, restart=args.outer_restart,
+                                inner_iters=args.inner_iters, max_iters=args.max_outer, reorth=args.reorth,
+                                spmm_rows=args.spmm_rows)
+    plain = ect.default_options(tol=1e-10, mode=ect.ECT_MODE_F64, restart=args.restart, max_iters=args.max_iters)
+    t0 = time.time()
+    dz_m, st_m = ctx.impedance(p.coils, p.z_pos, mixed)
+    t1 = time.time()
+    dz_p, st_p = ctx.impedance(p.coils, p.z_pos, plain)
+    t2 = time.time()
+    torch.cuda.synchronize()
+    err = float(np.abs(dz_m - dz_p).max() / np.abs(dz_p).max())
+    print(json.dumps({"dz_record": args.config, "n_nodes": p.mesh.n_nodes, "unknowns": 4 * p.mesh.n_nodes,
+                      "mixed_tol": args.tol, "fp64_tol": 1e-10, "dz_rel_err_mixed_vs_fp64": err,
+                      "dz_fp64": [[[float(z.real), float(z.imag)] for z in row] for row in dz_p[0]],
+                      "mixed": {"s": t1 - t0, "iters": st_m["iters"], "relres": st_m["relres_max"]},
+                      "fp64": {"s": t2 - t1, "iters": st_p["iters"], "relres": st_p["relres_max"]}}))
 
 
 def mlp_probe(args):
@@ -608,6 +644,8 @@ def main():
                     help="FP32 SpMM row tiling when not autotuned (0 auto, -1 unstaged)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel-probe", action="store_true", help="only launch the hot kernels on a mid-size case")
+    ap.add_argument("--dz-record", action="store_true",
+                    help="only compare Delta Z of the mixed solve (--tol) with the FP64 solve on --config")
     ap.add_argument("--probe-mg", action="store_true")
     ap.add_argument("--mlp-probe", action="store_true", help="only time the surrogate MLP on the tensor cores")
     ap.add_argument("--skip-plain", action="store_true")
@@ -620,6 +658,9 @@ def main():
     args = ap.parse_args()
     if args.kernel_probe:
         kernel_probe(args)
+        return
+    if args.dz_record:
+        dz_record(args)
         return
     if args.mlp_probe:
         mlp_probe(args)

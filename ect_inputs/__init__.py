@@ -212,39 +212,77 @@ def box_mesh(shape, lengths, block_shape=(2, 2, 4), jitter=0.0, seed=0):
                 lengths=tuple(lengths))
 
 
-def delaunay_box_mesh(shape, lengths, jitter=0.35, seed=0, block_nodes=8):
-    """Unstructured tetrahedral mesh of the box: the nodes of an nx x ny x nz
-    grid moved by U[-jitter*h, jitter*h] per axis (interior nodes freely, face
-    nodes within their face, edge nodes along their edge, corners fixed, so
-    the box faces stay planar), re-triangulated by Delaunay (scipy's Qhull)
-    and oriented positively.  No tet is a Kuhn tet and node valences vary.
+def unstructured_box_mesh(shape, lengths, jitter=0.12, seed=0, block_nodes=8):
+    """Unstructured tetrahedral mesh of the box, not a Kuhn mesh.
 
-    The nodes keep the grid's lexicographic order and block_of_node is a
-    placeholder (consecutive runs of block_nodes nodes); a partitioner
-    assigns the real subdomains and node order (see permute_mesh)."""
-    from scipy.spatial import Delaunay
+    Nodes: the nx x ny x nz grid plus one node at the centre of every cell.
+    Every quadrilateral cell face is cut along one of its two diagonals,
+    chosen at random per face (shared by the two cells of an interior face,
+    so the mesh is conforming), and every cell is filled by the 12 tets that
+    join its centre node to the 12 face triangles.  Then all nodes move by
+    U[-jitter*h, jitter*h] per axis (interior grid nodes and centres freely,
+    face nodes within their face, edge nodes along their edge, corners
+    fixed, so the box faces stay planar), and tets are oriented positively.
+    Valences vary from node to node (grid nodes touch 24 to 56 tets of
+    different shapes, centres 12), and every tet keeps a volume of order h^3.
 
-    base = box_mesh(shape, lengths, (1, 1, 1), jitter=0.0)
+    The nodes are numbered grid first (lexicographic), then centres, and
+    block_of_node is a placeholder (consecutive runs of block_nodes nodes);
+    a partitioner assigns the real subdomains and node order (permute_mesh)."""
     nx, ny, nz = shape
-    n = nx * ny * nz
-    # box_mesh with 1x1x1 blocks numbers nodes x-fastest, so node id = grid index
-    xyz = base.xyz.copy()
-    h = np.array(lengths, dtype=np.float64) / (np.array(shape) - 1)
-    on = [(base.bc_mask & bit) != 0 for bit in (BC_AX, BC_AY, BC_AZ)]
-    nfaces = on[0].astype(int) + on[1].astype(int) + on[2].astype(int)
+    L = np.array(lengths, dtype=np.float64)
+    h = L / (np.array(shape) - 1)
     rng = np.random.default_rng(seed)
-    d = rng.uniform(-jitter, jitter, size=(n, 3)) * h[None, :]
-    for a in range(3):
-        movable = (nfaces == 0) | ((nfaces >= 1) & (nfaces <= 2) & ~on[a])
-        xyz[:, a] += np.where(movable, d[:, a], 0.0)
-    tets = Delaunay(xyz).simplices.astype(np.int64)
+    gid = lambda i, j, k: i + nx * (j + ny * k)  # noqa: E731
+    k3, j3, i3 = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    gx = np.stack([i3.ravel(), j3.ravel(), k3.ravel()], axis=1).astype(np.float64)
+    ng = nx * ny * nz
+    ck, cj, ci = np.meshgrid(np.arange(nz - 1), np.arange(ny - 1), np.arange(nx - 1), indexing="ij")
+    cells = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1)
+    nc = cells.shape[0]
+    xyz = np.concatenate([gx, cells + 0.5]) * h[None, :] - 0.5 * L[None, :]
+    # diagonal choice per face: faces normal to axis a at grid plane index, keyed by the lower corner
+    diag = [rng.integers(0, 2, size=(nx, ny, nz)) for _ in range(3)]
+    tets = []
+    for c in range(nc):
+        i, j, k = cells[c]
+        centre = ng + c
+        for a in range(3):                       # the two faces normal to axis a
+            b1, b2 = [(1, 2), (0, 2), (0, 1)][a]
+            for side in (0, 1):
+                base = [i, j, k]
+                base[a] += side
+                def corner(u, v):
+                    q = list(base)
+                    q[b1] += u
+                    q[b2] += v
+                    return gid(*q)
+                q00, q10, q01, q11 = corner(0, 0), corner(1, 0), corner(0, 1), corner(1, 1)
+                if diag[a][tuple(base)]:
+                    tris = ((q00, q10, q11), (q00, q11, q01))
+                else:
+                    tris = ((q00, q10, q01), (q10, q11, q01))
+                for tri in tris:
+                    tets.append((tri[0], tri[1], tri[2], centre))
+    tets = np.array(tets, dtype=np.int64)
     vol = tet_volumes(xyz, tets)
     flip = vol < 0.0
     tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
-    if np.any(np.abs(vol) <= 1e-9 * float(np.prod(h))):
-        raise ValueError("degenerate tetrahedron in the Delaunay mesh (change the seed)")
+    # jitter (grid part keeps its face/edge/corner classes)
+    on = [np.concatenate([(gx[:, a] == 0) | (gx[:, a] == shape[a] - 1), np.zeros(nc, dtype=bool)])
+          for a in range(3)]
+    nfaces = on[0].astype(int) + on[1].astype(int) + on[2].astype(int)
+    d = rng.uniform(-jitter, jitter, size=xyz.shape) * h[None, :]
+    for a in range(3):
+        movable = (nfaces == 0) | ((nfaces >= 1) & (nfaces <= 2) & ~on[a])
+        xyz[:, a] += np.where(movable, d[:, a], 0.0)
+    vol = tet_volumes(xyz, tets)
+    if vol.min() <= 0.02 * float(np.prod(h)) / 12.0:
+        raise ValueError("jitter too large: a tetrahedron lost most of its volume")
+    bc = (on[0] * BC_AX + on[1] * BC_AY + on[2] * BC_AZ).astype(np.uint8)
+    n = xyz.shape[0]
     block = (np.arange(n) // block_nodes).astype(np.int32)
-    return Mesh(xyz=xyz, tets=tets.astype(np.int32), block_of_node=block, bc_mask=base.bc_mask.copy(),
+    return Mesh(xyz=xyz, tets=tets.astype(np.int32), block_of_node=block, bc_mask=bc,
                 shape=tuple(shape), block_shape=(block_nodes,), lengths=tuple(lengths))
 
 
@@ -416,7 +454,7 @@ def wall_loss_problem(shape, lengths, block_shape=(2, 2, 4), jitter=0.0, seed=0,
 
     Omega_d = tube-wall tets with centroid z in [-2, 2] mm and polar angle in
     [0, pi/2]; there the conductivity drops from 1e6 to sigma_d.  `mesh`
-    replaces the structured mesh (e.g. delaunay_box_mesh of the same box).
+    replaces the structured mesh (e.g. unstructured_box_mesh of the same box).
     """
     m = mesh if mesh is not None else box_mesh(shape, lengths, block_shape, jitter, seed)
     c = centroids(m)

@@ -1,8 +1,9 @@
 """GPU path on an unstructured mesh (Sec. 3, Steps 1-2 with a body of
-tetrahedra that is not a structured grid): a jittered point set re-
-triangulated by Delaunay, partitioned by the library's own recursive
-coordinate bisection (ect_partition) and renumbered; then assembly, mixed
-and FP64 solves and Delta Z against the CPU oracle.
+tetrahedra that is not a structured grid): grid nodes and cell centres,
+cells cut along randomly chosen face diagonals, all nodes jittered
+(ect_inputs.unstructured_box_mesh), partitioned by the library's own
+recursive coordinate bisection (ect_partition) and renumbered; then
+assembly, mixed and FP64 solves and Delta Z against the CPU oracle.
 
 The oracle works on the mesh in its original numbering (it never sees the
 library's partition); GPU results are mapped back through the permutation
@@ -28,7 +29,7 @@ def case():
     from paper_1602_03207_gb300 import build, ect
     build.build()
     ect.load_library()
-    m0 = E.delaunay_box_mesh((16, 16, 24), BOX, jitter=0.35, seed=4)
+    m0 = E.unstructured_box_mesh((12, 12, 18), BOX, seed=4)
     p0 = E.wall_loss_problem(None, BOX, z_pos=(0.5e-3,), mesh=m0)
     new_id, blk = ect.partition(m0.xyz, 16)
     p1 = E.wall_loss_problem(None, BOX, z_pos=(0.5e-3,), mesh=E.permute_mesh(m0, new_id, blk))

@@ -17,7 +17,7 @@ def ect():
 
 @pytest.mark.parametrize("s", [1, 5, 8, 16])
 def test_partition_is_a_valid_contiguous_blocking(ect, s):
-    m = E.delaunay_box_mesh((9, 8, 13), (20e-3, 20e-3, 40e-3), seed=2)
+    m = E.unstructured_box_mesh((9, 8, 13), (20e-3, 20e-3, 40e-3), seed=2)
     new_id, blk = ect.partition(m.xyz, s)
     n = m.n_nodes
     assert np.array_equal(np.sort(new_id), np.arange(n))                 # a permutation
@@ -65,7 +65,7 @@ def test_partition_rejects_bad_arguments(ect):
 
 
 def test_permuted_mesh_is_the_same_mesh():
-    m = E.delaunay_box_mesh((6, 7, 8), (1.0, 1.0, 1.0), seed=1)
+    m = E.unstructured_box_mesh((6, 7, 8), (1.0, 1.0, 1.0), seed=1)
     rng = np.random.default_rng(0)
     new_id = rng.permutation(m.n_nodes)
     pm = E.permute_mesh(m, new_id, np.zeros(m.n_nodes, dtype=np.int32))
@@ -74,8 +74,8 @@ def test_permuted_mesh_is_the_same_mesh():
     np.testing.assert_allclose(E.tet_volumes(pm.xyz, pm.tets), E.tet_volumes(m.xyz, m.tets))
 
 
-def test_delaunay_mesh_fills_the_box_and_is_not_kuhn():
-    m = E.delaunay_box_mesh((7, 6, 9), (2.0, 1.0, 3.0), seed=5)
+def test_unstructured_mesh_fills_the_box_and_is_not_kuhn():
+    m = E.unstructured_box_mesh((7, 6, 9), (2.0, 1.0, 3.0), seed=5)
     vol = E.tet_volumes(m.xyz, m.tets)
     assert vol.min() > 0 and abs(vol.sum() - 6.0) < 1e-12
     # box faces stay planar (A.n = 0 needs them) and the face masks match the coordinates
@@ -83,17 +83,25 @@ def test_delaunay_mesh_fills_the_box_and_is_not_kuhn():
         on = (m.bc_mask & bit) != 0
         assert np.allclose(np.abs(m.xyz[on, a]), 0.5 * m.lengths[a], rtol=0, atol=1e-15)
         assert np.all(np.abs(np.abs(m.xyz[~on, a]) - 0.5 * m.lengths[a]) > 1e-9)
-    # node valences vary (a Kuhn mesh has 15-node stencils inside)
+    # every cell's 12 tets share its centre node; node valences vary (a Kuhn mesh has
+    # 15-node stencils everywhere inside)
     G = np.zeros(m.n_nodes, dtype=int)
     pairs = {(min(a, b), max(a, b)) for t in m.tets for a in t for b in t if a != b}
     for a, b in pairs:
         G[a] += 1
         G[b] += 1
     assert len(set(G.tolist())) > 5
+    # conforming: every interior triangle is shared by exactly two tets
+    from collections import Counter
+    faces = Counter(tuple(sorted((int(t[a]), int(t[b]), int(t[c])))) for t in m.tets
+                    for a, b, c in ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)))
+    assert max(faces.values()) == 2
+    on_box = lambda f: any(np.all(np.isclose(np.abs(m.xyz[list(f), a]), 0.5 * m.lengths[a])) for a in range(3))  # noqa
+    assert all(on_box(f) for f, n in faces.items() if n == 1)
 
 
 def test_tetgen_round_trip_and_one_based_files(tmp_path):
-    m = E.delaunay_box_mesh((5, 5, 6), (1.0, 1.0, 1.0), seed=3)
+    m = E.unstructured_box_mesh((5, 5, 6), (1.0, 1.0, 1.0), seed=3)
     region = np.arange(m.n_tets) % 3
     E.write_tetgen(str(tmp_path / "m"), m, region)
     xyz, tets, bc, reg = E.read_tetgen(str(tmp_path / "m"))

@@ -219,7 +219,8 @@ def run_gpu(args):
             ms_pair = ctx.solve(0, Bsrc, U0, k, o)["ms"] + ctx.solve(1, Bsrc, Ud, k, o)["ms"]
             if best_ms is None or ms_pair < best_ms:
                 mixed, best_ms = o, ms_pair
-        tune = {"rhs_tile": mixed.rhs_tile, "restart": mixed.restart, "inner_iters": mixed.inner_iters,
+        tune = {"rhs_tile": mixed.rhs_tile, "spmm_rows": mixed.spmm_rows, "restart": mixed.restart,
+                "inner_iters": mixed.inner_iters,
                 "reorth": mixed.reorth, "seconds": time.time() - t_at, "pair_ms": best_ms,
                 "tuned_on": "vacuum and defect systems; the faster option set on both"}
 

@@ -77,8 +77,9 @@ typedef struct {
                            first removed more than half of ||w||^2 (default); 2: as 1 in
                            the FP64 loop, one classical pass in the mixed mode's FP32 loop;
                            3: one classical pass in both loops                           */
-    int spmm_rows;      /* FP32 SpMM row tiling: block rows per shared-memory-staged tile
-                           (0 = auto, 16); -1 = the unstaged kernels (x gathered from L1/L2) */
+    int spmm_rows;      /* FP32 SpMM variant: > 0 block rows per shared-memory-staged tile;
+                           0 = auto (32); -1 = one thread per scalar row (x gathered from
+                           L1/L2); -2 = one warp per block row over the transposed blocks */
 } ect_options;
 
 typedef struct {
@@ -189,6 +190,14 @@ int ect_assemble(ect_ctx* ctx, int which, int precision_mask);
  * coarse corrections. */
 int ect_precond_setup(ect_ctx* ctx, int which, int precision_mask, int coarse_group);
 
+/* Cut every subdomain of the mesh into `parts` (1, 2 or 4) contiguous
+ * smoothing blocks of near-equal size: the blocks of the block-Jacobi sweeps
+ * and the first aggregates of the multigrid hierarchy (the subdomain size s
+ * of the preconditioner).  Every preconditioner must be set up again
+ * (ect_precond_setup).  1 = the mesh's subdomains (the default). */
+int ect_set_block_split(ect_ctx* ctx, int parts);
+int ect_get_block_split(const ect_ctx* ctx);
+
 /* Sizes of the assembled pattern: rows = n_nodes block rows, nnzb blocks. */
 int ect_matrix_info(const ect_ctx* ctx, int64_t* n_block_rows, int64_t* nnzb);
 
@@ -208,8 +217,9 @@ int ect_spmv(ect_ctx* ctx, int which, int precision, const void* d_x, void* d_y,
 
 /* Row tiling of the shared-memory-staged FP32 SpMM used by the kernel-level
  * calls ect_spmv (ECT_F32) and ect_precond_apply (ECT_F32, multigrid
- * preconditioner): rows block rows per tile (0 = auto, 16; at most 64);
- * -1 = the unstaged kernels.  Solves take ect_options.spmm_rows instead. */
+ * preconditioner): rows block rows per tile (0 = auto, 32; at most 64);
+ * -1 = one thread per scalar row; -2 = one warp per block row.  Solves take
+ * ect_options.spmm_rows instead. */
 int ect_set_spmm_rows(ect_ctx* ctx, int rows);
 
 /* z = P^-1 r on the scaled system for k vectors ([k][n][4]): the
@@ -241,11 +251,17 @@ int ect_solve(ect_ctx* ctx, int which, const void* d_rhs, void* d_x, int k,
 
 /* Autotuner for batched solves of `which` with k right-hand sides d_rhs
  * (complex128 [k][n_nodes][4]): times the SpMM and preconditioner right-hand-
- * side tile (1, 2, 4, 8) with CUDA events, then runs full solves of d_rhs for
+ * side tile (1, 2, 4, 8) with CUDA events, in mixed mode also the FP32 SpMM
+ * variant and row tiling (spmm_rows 32, 24, 16, -1, -2), then runs full solves of d_rhs for
  * each (restart, inner_iters) candidate of the mode in *base and keeps the
  * fastest that converges; in mixed mode the winner is also tried with reorth
- * = 2 and 3.  *best receives *base with rhs_tile, restart, inner_iters and reorth
- * replaced; stats of the winning solve go to *stats (may be NULL).
+ * = 2 and 3; last, the subdomains are cut into 1 and 2 smoothing blocks
+ * (ect_set_block_split) with the preconditioner rebuilt and the winner's
+ * solve timed again.  *best receives *base with rhs_tile, spmm_rows, restart,
+ * inner_iters and reorth replaced; the best subdomain split stays applied to
+ * the context (ect_get_block_split) and every preconditioner that was set up
+ * before the call is set up again for it.  Stats of the winning solve go to
+ * *stats (may be NULL).
  * d_work: complex128 [k][n_nodes][4] scratch for the solutions.  Costs one
  * full solve per candidate; call it once per workload. */
 int ect_autotune(ect_ctx* ctx, int which, const void* d_rhs, void* d_work, int k, const ect_options* base,

@@ -201,7 +201,7 @@ int ect_spmv(ect_ctx* c, int which, int precision, const void* d_x, void* d_y, i
 int ect_set_spmm_rows(ect_ctx* c, int rows) {
     if (!c) return ECT_ERR_ARG;
     return guarded(c, [&] {
-        ECT_REQUIRE(rows == -1 || (rows >= 0 && rows <= 64), ECT_ERR_ARG, "rows must be -1 or in [0, 64]");
+        ECT_REQUIRE(rows >= -2 && rows <= 64, ECT_ERR_ARG, "rows must be -2, -1 or in [0, 64]");
         c->kernel_rows = rows == 0 ? STAGED_ROWS_DEFAULT : rows;
     });
 }
@@ -297,6 +297,34 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
             }
         }
         o.rhs_tile = best_tile;
+        // 1b. FP32 SpMM variant and row tiling (mixed mode): the Krylov product plus one
+        //     preconditioner application, each candidate with its plans built
+        if (mixed) {
+            float best_rows_ms = 1e30f;
+            int best_rows = o.spmm_rows;
+            for (int rows : {0, 24, 16, -1, -2}) {
+                c->staged_rows = rows == 0 ? STAGED_ROWS_DEFAULT : rows;
+                staged_prepare(c, which);
+                auto run = [&] {
+                    spmv_f32(c, which, a.as<float2>(), b.as<float2>(), k, ld, o.rhs_tile, nullptr);
+                    precond_apply_f32(c, which, b.as<float2>(), a.as<float2>(), k, ld, o.rhs_tile, nullptr);
+                };
+                run();
+                ECT_CUDA(cudaEventRecord(c->ev0, st));
+                for (int r = 0; r < 5; ++r) run();
+                ECT_CUDA(cudaEventRecord(c->ev1, st));
+                ECT_CUDA(cudaEventSynchronize(c->ev1));
+                float ms = 0.f;
+                ECT_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+                if (ms < best_rows_ms) {
+                    best_rows_ms = ms;
+                    best_rows = rows;
+                }
+            }
+            ECT_REQUIRE(!staged_take_error(st), ECT_ERR_TIMEOUT,
+                        "a bounded wait for a bulk copy expired in the staged SpMM");
+            o.spmm_rows = best_rows;
+        }
         // 2. Krylov lengths: full solves, fastest converged wins
         std::vector<std::pair<int, int>> cand;
         if (mixed) cand = {{10, 10}, {10, 20}, {8, 30}, {16, 12}, {16, 16}, {12, 24}, {16, 20}, {16, 24}};
@@ -344,10 +372,51 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
                 }
             }
         }
+        // 3. subdomain size: each subdomain cut into `parts` smoothing blocks (also the first
+        //    multigrid aggregates), the preconditioner rebuilt, the winner's solve timed again
+        {
+            const int n_mat = 2 + (int)c->smat.size();
+            std::vector<char> had(n_mat, 0);
+            for (int m = 0; m < n_mat; ++m) had[m] = ctx_mat(c, m).pc_f64;
+            const int start = c->block_split;
+            int best_parts = start;
+            for (int parts : {1, 2}) {
+                if (parts == start) continue;
+                set_block_split(c, parts);
+                precond_setup(c, which, M.pc_mask, M.pc_group);
+                coarse_scratch(c, which, k);
+                ect_stats s{};
+                try {
+                    solve(c, which, (const double2*)d_rhs, (double2*)d_work, k, win, &s);
+                    if (s.ms < best_t) {
+                        best_t = s.ms;
+                        best_parts = parts;
+                        wst = s;
+                    }
+                } catch (const EctError& e) {
+                    if (e.code != ECT_ERR_NOT_CONVERGED && e.code != ECT_ERR_TIMEOUT) throw;
+                }
+            }
+            if (c->block_split != best_parts || best_parts != start) {
+                set_block_split(c, best_parts);
+                for (int m = 0; m < n_mat; ++m)
+                    if (had[m] || m == which) {
+                        Matrix& Mm = ctx_mat(c, m);
+                        precond_setup(c, m, Mm.pc_mask, Mm.pc_group);
+                    }
+            }
+        }
         *best = win;
         if (stats) *stats = wst;
     });
 }
+
+int ect_set_block_split(ect_ctx* c, int parts) {
+    if (!c) return ECT_ERR_ARG;
+    return guarded(c, [&] { set_block_split(c, parts); });
+}
+
+int ect_get_block_split(const ect_ctx* c) { return c ? c->block_split : 0; }
 
 int ect_assemble_sweep(ect_ctx* c, const double* freq_hz, int n_freq, int precision_mask) {
     if (!c) return ECT_ERR_ARG;

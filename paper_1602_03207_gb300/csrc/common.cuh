@@ -212,8 +212,15 @@ void bsr_spmm_staged_f32(cudaStream_t st, const StagedPlan& P, const int32_t* rp
 // Read and clear the flag that a staged kernel sets when its bounded wait on
 // a bulk copy expired (1 = expired).  Synchronises the stream.
 int staged_take_error(cudaStream_t st);
+// FP32 SpMM with one warp per block row: lane (p, q) takes column p of every
+// block (from the transposed copy) and right-hand side q, and the four
+// partial rows are summed with shuffles at the end of the row (spmv.cu)
+void bsr_spmm_colwarp_f32(cudaStream_t st, const int32_t* rp, const int32_t* col, const float2* valt, int64_t N,
+                          const float2* x, int64_t ldx, const float2* b, float2* y, int64_t ldy, int k,
+                          const int* active);
+constexpr int SPMM_COLWARP = -2;  // ect_options.spmm_rows value selecting it
 // default target rows per tile of the staged SpMM
-constexpr int STAGED_ROWS_DEFAULT = 16;
+constexpr int STAGED_ROWS_DEFAULT = 32;
 
 // ----------------------------------------------------------------------------
 // context
@@ -233,6 +240,7 @@ struct Matrix {
     DevBuf sval;           // double2[nnzb*16] scaled  S = T M T
     DevBuf sval32;         // float2 [nnzb*16] scaled
     DevBuf sval32lo;       // float2 [nnzb*16] FP32 remainder: sval ~= sval32 + sval32lo to ~2^-48
+    DevBuf sval32t;        // float2 [nnzb*16] FP32 scaled, each block transposed (column-major)
     DevBuf t;              // double[4N] scaling
     DevBuf pinv;           // double2 block inverses (column-major per block)
     DevBuf pinv32;         // float2  block inverses
@@ -250,6 +258,7 @@ struct Matrix {
     std::vector<uint8_t> h_fix;   // host copy of fixmask
     std::vector<double> h_sigma, h_nu;  // per-tet coefficients of this configuration (host)
     // impedance boundary condition (Eq. IBC): plate tets removed, surface term on their boundary
+    int pc_mask = 0, pc_group = 0;  // arguments of the last ect_precond_setup
     bool ibc = false;
     double ibc_sigma = 0.0, ibc_nu = 0.0;  // plate conductivity and 1/mu
     std::vector<uint8_t> h_void;  // per tet: 1 = plate (removed from the volume forms)
@@ -275,7 +284,7 @@ struct Matrix {
         h_void.clear();
         n_faces = 0;
         for (DevBuf* b : {&tvoid, &s_ptr, &s_ent, &s_geo}) b->release();
-        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &sval32lo, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
+        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &sval32lo, &sval32t, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
                           &agg_lo, &agg_hi, &zv, &zv32, &rc, &zc, &gpart})
             b->release();
     }
@@ -311,7 +320,9 @@ struct ect_ctx {
     int64_t pinv_total32 = 0;
     DevBuf omega_d;        // int32 list of defect tets
     int64_t n_omega_d = 0;
-    std::vector<int32_t> h_block_ptr;
+    std::vector<int32_t> h_block_ptr;       // smoothing blocks (the subdomains, possibly split)
+    std::vector<int32_t> h_block_ptr_mesh;  // the subdomains given with the mesh
+    int block_split = 1;                    // pieces per subdomain
     std::vector<int32_t> h_row_ptr, h_col;
     std::vector<int32_t> h_tets;
     std::vector<uint8_t> h_bc;
@@ -424,6 +435,10 @@ void delta_z(ect_ctx* c, const double2* u0, const double2* ud, const double2* b,
              int n_pos, double* h_dz, double* h_dz_emf, double omega = 0.0);
 // drop the frequency-sweep matrices (their coefficients changed)
 void clear_sweep(ect_ctx* c);
+// smoothing blocks from the mesh's subdomains and c->block_split (mesh_setup.cu)
+void apply_block_split(ect_ctx* c);
+// cut every subdomain into `parts` pieces; every preconditioner must be set up again
+void set_block_split(ect_ctx* c, int parts);
 void solve(ect_ctx* c, int which, const double2* rhs, double2* x, int k, const ect_options& opt,
            ect_stats* st);
 // all sweep frequencies of configuration `config` in one lockstep solve: rhs, x [F][k][4N]

@@ -783,7 +783,7 @@ void solve_groups(ect_ctx* c, const Groups& G, const double2* rhs, double2* x, i
             ECT_REQUIRE(M.has_f32 && M.pc_f32, ECT_ERR_STATE, "mixed mode needs the FP32 matrix and preconditioner");
     }
     cudaStream_t st = c->stream;
-    ECT_REQUIRE(opt.spmm_rows >= -1 && opt.spmm_rows <= 64, ECT_ERR_ARG, "spmm_rows must be -1 or in [0, 64]");
+    ECT_REQUIRE(opt.spmm_rows >= -2 && opt.spmm_rows <= 64, ECT_ERR_ARG, "spmm_rows must be -2, -1 or in [0, 64]");
     c->staged_rows = opt.spmm_rows == 0 ? STAGED_ROWS_DEFAULT : opt.spmm_rows;
     if (opt.mode == ECT_MODE_MIXED)
         for (const Group& g : G) staged_prepare(c, g.which);

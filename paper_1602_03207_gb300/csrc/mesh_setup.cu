@@ -200,6 +200,54 @@ void upload_defect_list(ect_ctx* c, const std::vector<double>& s1, const std::ve
 
 }  // namespace
 
+// The smoothing blocks (and first multigrid aggregates): the mesh's subdomains,
+// each cut into c->block_split contiguous pieces of near-equal size.
+void apply_block_split(ect_ctx* c) {
+    const std::vector<int32_t>& mb = c->h_block_ptr_mesh;
+    std::vector<int32_t> bptr(1, 0);
+    for (size_t b = 0; b + 1 < mb.size(); ++b) {
+        const int n = mb[b + 1] - mb[b];
+        const int parts = std::min(c->block_split, n);
+        for (int q = 1; q <= parts; ++q) bptr.push_back(mb[b] + (int32_t)((int64_t)n * q / parts));
+    }
+    int maxb = 0;
+    std::vector<int64_t> poff(bptr.size(), 0), poff32(bptr.size(), 0);
+    for (size_t b = 0; b + 1 < bptr.size(); ++b) {
+        const int sz = bptr[b + 1] - bptr[b];
+        maxb = std::max(maxb, sz);
+        poff[b + 1] = poff[b] + (int64_t)(4 * sz) * (4 * sz);
+        poff32[b + 1] = poff32[b] + sym_packed_size(4 * sz);
+    }
+    c->n_blocks = (int64_t)bptr.size() - 1;
+    c->max_block_nodes = maxb;
+    c->h_block_ptr = bptr;
+    c->pinv_total = poff.back();
+    c->pinv_total32 = poff32.back();
+    cudaStream_t st = c->stream;
+    c->block_ptr.alloc(sizeof(int32_t) * bptr.size());
+    c->pinv_off.alloc(sizeof(int64_t) * poff.size());
+    c->pinv_off32.alloc(sizeof(int64_t) * poff32.size());
+    ECT_CUDA(cudaMemcpyAsync(c->block_ptr.p, bptr.data(), c->block_ptr.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(c->pinv_off.p, poff.data(), c->pinv_off.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaMemcpyAsync(c->pinv_off32.p, poff32.data(), c->pinv_off32.bytes, cudaMemcpyHostToDevice, st));
+    ECT_CUDA(cudaStreamSynchronize(st));
+}
+
+void set_block_split(ect_ctx* c, int parts) {
+    ECT_REQUIRE(c->mesh_set, ECT_ERR_STATE, "ect_set_mesh must come first");
+    ECT_REQUIRE(parts == 1 || parts == 2 || parts == 4, ECT_ERR_ARG, "parts must be 1, 2 or 4");
+    if (parts == c->block_split) return;
+    workspace_free(c);
+    auto invalidate = [](Matrix& M) {
+        mg_free(M);
+        M.pc_f64 = M.pc_f32 = false;
+    };
+    for (int m = 0; m < 2; ++m) invalidate(c->mat[m]);
+    for (Matrix& M : c->smat) invalidate(M);
+    c->block_split = parts;
+    apply_block_split(c);
+}
+
 void clear_sweep(ect_ctx* c) {
     workspace_free(c);
     c->smat.clear();
@@ -238,13 +286,7 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     }
     bptr.push_back((int32_t)n_nodes);
     int maxb = 0;
-    std::vector<int64_t> poff(bptr.size(), 0), poff32(bptr.size(), 0);
-    for (size_t b = 0; b + 1 < bptr.size(); ++b) {
-        int sz = bptr[b + 1] - bptr[b];
-        maxb = std::max(maxb, sz);
-        poff[b + 1] = poff[b] + (int64_t)(4 * sz) * (4 * sz);
-        poff32[b + 1] = poff32[b] + sym_packed_size(4 * sz);
-    }
+    for (size_t b = 0; b + 1 < bptr.size(); ++b) maxb = std::max(maxb, bptr[b + 1] - bptr[b]);
     ECT_REQUIRE(maxb <= 16, ECT_ERR_ARG, "a subdomain block has more than 16 nodes");
 
     // effective coefficients of the two configurations
@@ -259,25 +301,17 @@ void mesh_setup(ect_ctx* c, const double* xyz, int64_t n_nodes, const int32_t* t
     c->fine_plan.reset();
     c->n_nodes = n_nodes;
     c->n_tets = n_tets;
-    c->n_blocks = (int64_t)bptr.size() - 1;
-    c->max_block_nodes = maxb;
-    c->h_block_ptr = bptr;
-    c->pinv_total = poff.back();
-    c->pinv_total32 = poff32.back();
+    c->h_block_ptr_mesh = bptr;
+    c->block_split = 1;
     cudaStream_t st = c->stream;
 
     c->xyz.alloc(sizeof(double) * 3 * n_nodes);
     c->tets.alloc(sizeof(int32_t) * 4 * n_tets);
     c->bc.alloc(n_nodes);
-    c->block_ptr.alloc(sizeof(int32_t) * bptr.size());
-    c->pinv_off.alloc(sizeof(int64_t) * poff.size());
-    c->pinv_off32.alloc(sizeof(int64_t) * poff32.size());
     ECT_CUDA(cudaMemcpyAsync(c->xyz.p, xyz, c->xyz.bytes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->tets.p, tets, c->tets.bytes, cudaMemcpyHostToDevice, st));
     ECT_CUDA(cudaMemcpyAsync(c->bc.p, bc_mask, n_nodes, cudaMemcpyHostToDevice, st));
-    ECT_CUDA(cudaMemcpyAsync(c->block_ptr.p, bptr.data(), c->block_ptr.bytes, cudaMemcpyHostToDevice, st));
-    ECT_CUDA(cudaMemcpyAsync(c->pinv_off.p, poff.data(), c->pinv_off.bytes, cudaMemcpyHostToDevice, st));
-    ECT_CUDA(cudaMemcpyAsync(c->pinv_off32.p, poff32.data(), c->pinv_off32.bytes, cudaMemcpyHostToDevice, st));
+    apply_block_split(c);
     c->h_tets.assign(tets, tets + 4 * n_tets);
     c->h_bc.assign(bc_mask, bc_mask + n_nodes);
     c->h_sigma0 = s0;

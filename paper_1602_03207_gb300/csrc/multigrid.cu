@@ -246,6 +246,7 @@ struct Multigrid {
     int64_t kcap = 0;
     bool f32 = false;
     const StagedPlan* fine_plan = nullptr;   // the context's plan of the finest pattern
+    const float2* val32t = nullptr;          // transposed FP32 blocks of the finest matrix
     int staged_rows = -1;                    // rows per staged tile the level plans were built for
 };
 
@@ -634,8 +635,12 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
     // levels (few rows, many blocks per row: the warp splits the row's serial chain of loads)
     const StagedPlan* plan = l == 0 ? G->fine_plan : &L.plan;
     const bool staged = std::is_same<T, float>::value && G->staged_rows > 0 && plan && plan->ok;
+    const bool colwarp = std::is_same<T, float>::value && G->staged_rows == SPMM_COLWARP && l == 0 && G->val32t;
     auto residual = [&]() {
-        if (staged && L.n > WARP_ROW_MAX_NODES)
+        if (colwarp)
+            bsr_spmm_colwarp_f32(st, L.rp, L.col, G->val32t, L.n, (const float2*)z, ld, (const float2*)r, (float2*)t,
+                                 ld, k, active);
+        else if (staged && L.n > WARP_ROW_MAX_NODES)
             bsr_spmm_staged_f32(st, *plan, L.rp, (const float2*)val, (const float2*)z, ld, (const float2*)r,
                                 (float2*)t, ld, k, active);
         else if (L.n <= WARP_ROW_MAX_NODES)
@@ -687,9 +692,13 @@ void mg_apply_f32(ect_ctx* c, int which, const float2* r, float2* z, int k, int6
 
 void staged_prepare(ect_ctx* c, int which) {
     const int rows = c->staged_rows;
-    Multigrid* G = ctx_mat(c, which).mg;
+    Matrix& M = ctx_mat(c, which);
+    Multigrid* G = M.mg;
     if (rows <= 0) {
-        if (G) G->staged_rows = -1;
+        if (G) {
+            G->staged_rows = rows == SPMM_COLWARP ? SPMM_COLWARP : -1;
+            G->val32t = M.sval32t.as<float2>();
+        }
         return;
     }
     cudaStream_t st = c->stream;

@@ -270,6 +270,114 @@ __global__ void __launch_bounds__(64) k_block_apply_sym(const int32_t* __restric
         }
 }
 
+// Paired single-precision FMA (two lanes of a 64-bit register pair per
+// instruction, sm_100 family): d = a * b + c elementwise.
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// k_block_apply_sym for a full tile of 8 right-hand sides with paired FMAs.
+// The tile is kept planar in shared memory (real parts of the 8 right-hand
+// sides of a row, then their imaginary parts), so two right-hand sides are
+// one 64-bit register pair; with the entry a of the inverse broadcast into
+// pairs, a complex multiply-add of two right-hand sides is four paired FMAs:
+//   re += (a.x, a.x) (r.re) + (-a.y, -a.y) (r.im),  im += (a.x, a.x) (r.im) + (a.y, a.y) (r.re).
+// Half the FMA instructions of the scalar form for the same shared-memory
+// loads (the limiting resource of the scalar form was the issue rate).
+__global__ void __launch_bounds__(64) k_block_apply_sym8x2(const int32_t* __restrict__ block_ptr,
+                                                          const int64_t* __restrict__ poff,
+                                                          const float2* __restrict__ pinv, const float2* __restrict__ r,
+                                                          float2* __restrict__ z, int k, int64_t ld,
+                                                          const int* __restrict__ active,
+                                                          const int32_t* __restrict__ blk_c,
+                                                          const float2* __restrict__ zc, int64_t nc,
+                                                          const float* __restrict__ zv, int accumulate, int ntile) {
+    constexpr int KT = 8;
+    __shared__ float4 S4[SYM_MAX_F4];
+    __shared__ __align__(16) float rre[64][KT];
+    __shared__ __align__(16) float rim[64][KT];
+    const int blk = (int)(blockIdx.x / ntile), tid = threadIdx.x;
+    const int r0 = (int)(blockIdx.x % ntile) * KT;
+    const int n0 = block_ptr[blk], n1 = block_ptr[blk + 1];
+    const int b = 4 * (n1 - n0);
+    const int64_t base = 4 * (int64_t)n0;
+    const int n4 = b * (b + 1) / 4;
+    unsigned onm = 0;
+#pragma unroll
+    for (int q = 0; q < KT; ++q) onm |= ((r0 + q < k) && (!active || active[r0 + q])) ? 1u << q : 0u;
+    if (!onm) return;  // the whole tile has retired (uniform over the CTA, before any barrier)
+    const float4* P4 = reinterpret_cast<const float4*>(pinv + poff[blk]);
+    for (int e = tid; e < n4; e += 64) S4[e] = __ldg(P4 + e);
+    for (int f = tid; f < 64 * KT; f += 64) {
+        const int row = f / KT, q = f - row * KT;
+        float2 v = make_float2(0.f, 0.f);
+        if (row < b && ((onm >> q) & 1u)) v = r[(int64_t)(r0 + q) * ld + base + row];
+        rre[row][q] = v.x;
+        rim[row][q] = v.y;
+    }
+    __syncthreads();
+    if (tid >= b) return;
+    const float2* S = reinterpret_cast<const float2*>(S4);
+    unsigned long long are[4], aim[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) are[h] = aim[h] = 0ull;
+    const int ti = tid * (tid + 1) / 2;
+    int tj = 0;  // j (j + 1) / 2
+#pragma unroll 2
+    for (int j = 0; j < b; ++j) {
+        const float2 a = S[j >= tid ? tj + tid : ti + j];
+        const unsigned long long ax = f2pack(a.x, a.x), ay = f2pack(a.y, a.y), nay = f2pack(-a.y, -a.y);
+        const ulonglong2 re01 = *reinterpret_cast<const ulonglong2*>(&rre[j][0]);
+        const ulonglong2 re23 = *reinterpret_cast<const ulonglong2*>(&rre[j][4]);
+        const ulonglong2 im01 = *reinterpret_cast<const ulonglong2*>(&rim[j][0]);
+        const ulonglong2 im23 = *reinterpret_cast<const ulonglong2*>(&rim[j][4]);
+        const unsigned long long vr[4] = {re01.x, re01.y, re23.x, re23.y};
+        const unsigned long long vi[4] = {im01.x, im01.y, im23.x, im23.y};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            are[h] = ffma2(ax, vr[h], are[h]);
+            are[h] = ffma2(nay, vi[h], are[h]);
+            aim[h] = ffma2(ax, vi[h], aim[h]);
+            aim[h] = ffma2(ay, vr[h], aim[h]);
+        }
+        tj += j + 1;
+    }
+    float2 acc[KT];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        f2unpack(are[h], acc[2 * h].x, acc[2 * h + 1].x);
+        f2unpack(aim[h], acc[2 * h].y, acc[2 * h + 1].y);
+    }
+    if (zc && (tid & 3) == 3) {
+        const int cc = blk_c[blk];
+        const float w = zv[n0 + (tid >> 2)];
+        if (cc >= 0 && w != 0.f)
+#pragma unroll
+            for (int q = 0; q < KT; ++q) {
+                if (!((onm >> q) & 1u)) continue;
+                const float2 v = zc[(int64_t)(r0 + q) * nc + cc];
+                acc[q].x += w * v.x;
+                acc[q].y += w * v.y;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < KT; ++q)
+        if ((onm >> q) & 1u) {
+            float2* zp = z + (int64_t)(r0 + q) * ld + base + tid;
+            *zp = accumulate ? cadd(*zp, acc[q]) : acc[q];
+        }
+}
+
 // coarse restriction: rc[r][c] = sum over the group's nodes of zv[i] * r[r][4i+3]
 template <typename T>
 __global__ void __launch_bounds__(128) k_coarse_restrict(const C<T>* __restrict__ r, int64_t ld,
@@ -438,7 +546,7 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
     const int32_t* bc = M.blk_c.as<int32_t>();
     if constexpr (std::is_same<T, float>::value) {
         switch (kt) {
-            case 8: k_block_apply_sym<8><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            case 8: k_block_apply_sym8x2<<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
             case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
             case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
             default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
@@ -570,7 +678,7 @@ void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, cons
     const int acc = accumulate ? 1 : 0;
     if constexpr (std::is_same<T, float>::value) {
         switch (kt) {
-            case 8: k_block_apply_sym<8><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            case 8: k_block_apply_sym8x2<<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
             case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
             case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
             default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
@@ -641,6 +749,8 @@ void precond_setup(ect_ctx* c, int which, int precision_mask, int coarse_group) 
     ECT_REQUIRE(which_valid(c, which), ECT_ERR_ARG, "bad which");
     Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.assembled, ECT_ERR_STATE, "ect_assemble must come before ect_precond_setup");
+    M.pc_mask = precision_mask;
+    M.pc_group = coarse_group;
     bool f32 = (precision_mask & ECT_F32) != 0;
     cudaStream_t st = c->stream;
     M.pinv.alloc(sizeof(double2) * c->pinv_total);

@@ -1,31 +1,36 @@
 // Kernel (b), staged form: BSR (4x4 complex FP32 blocks) SpMM for up to 8
 // right-hand sides per work item, with the operands staged in shared memory
-// by a persistent, software-pipelined CTA per SM.
+// by a persistent, warp-specialised pipeline (one CTA per SM).
 //
 // The rows of the matrix are cut into tiles of consecutive block rows (the
 // subdomain-major node order makes a tile a compact piece of the mesh).  For
-// each tile the plan holds its metadata record (the row offsets and, per
-// block, the position of the block's column node in the tile's column list)
+// each tile the plan holds its metadata record (its row range, the row
+// offsets and, per block, the position of the block's column node in the
+// tile's column list)
 // and the column list itself, which covers the tile's distinct column nodes
 // with runs of consecutive nodes.  A work item is (tile, tile of 8 right-hand
 // sides).  Each CTA walks the items b, b + G, b + 2G, ... through a ring of S
-// shared-memory stages, S - 1 items ahead of the one it computes:
-//   * one thread starts two bulk copies (TMA engine) per item: the tile's
-//     blocks (a contiguous nnz_tile x 128 bytes) and its metadata record,
-//     completing on the stage's mbarrier;
-//   * every thread copies the x values of one (column node, half) of the list
-//     for the 8 right-hand sides with 16-byte asynchronous copies (x is laid
-//     out [rhs q][column][4 complex] in the stage; list entries are mostly
-//     consecutive nodes, so a warp's copies are contiguous runs); the node
-//     index is loaded one item earlier still, so no copy waits for it;
-//   * compute: one warp per block row; lane (p, q) owns scalar row p of
-//     right-hand side q, reads row p of each block and the 4 values of x_q at
-//     the block's column node from shared memory (conflict-free), keeps one
-//     complex accumulator and stores y (or b - A x) directly.
-// The matrix streams from HBM while earlier stages are being computed, every
-// x value of a tile's list is read once per item, and no gather goes through
-// L1.  The mbarrier wait is bounded: on expiry the CTA sets a device flag
-// (read by staged_take_error) and leaves.
+// shared-memory stages:
+//   * producer warps: once an item's stage is free, one thread starts two
+//     bulk copies (TMA engine) of the tile's blocks (a contiguous nnz_tile x
+//     128 bytes) and of its metadata record, and the producer threads copy
+//     the x values of every (column node, half) of the list for the 8
+//     right-hand sides with 16-byte asynchronous copies (x is laid out [rhs
+//     q][column][4 complex] in the stage; list entries are mostly consecutive
+//     nodes, so a warp's copies are contiguous runs); all of it completes on
+//     the stage's "full" mbarrier;
+//   * consumer warps: two block rows per warp, the half-warps on alternate
+//     blocks of a row; lane (pp, qq) of an eight-lane group owns scalar rows
+//     2pp, 2pp + 1 of right-hand sides 2qq, 2qq + 1,
+//     reads those two rows of each block and the x values of its two right-
+//     hand sides at the block's column node from shared memory (one 16-byte
+//     load feeds two outputs), keeps four complex accumulators and stores y
+//     (or b - A x) directly, then the warp arrives on the stage's "empty"
+//     mbarrier.
+// There is no CTA-wide barrier in the loop: the matrix streams from HBM while
+// earlier stages are computed, every x value of a tile's list is read once
+// per item, and no gather goes through L1.  All waits are bounded: on expiry
+// a thread sets a device flag (read by staged_take_error) and leaves.
 #include <algorithm>
 #include <numeric>
 
@@ -35,12 +40,16 @@
 namespace {
 
 constexpr int STG_KT = 8;                // right-hand sides per work item
-constexpr int STG_WARPS = 16;
+constexpr int PRODUCER_WARPS = 4;       // stage the next items
+constexpr int CONSUMER_WARPS = 20;      // compute: two block rows per warp at a time
+constexpr int STG_WARPS = PRODUCER_WARPS + CONSUMER_WARPS;
 constexpr int STG_THREADS = 32 * STG_WARPS;
+constexpr int PRODUCER_THREADS = 32 * PRODUCER_WARPS;
 constexpr int MAX_STAGES = 4;
 constexpr int MAX_TILE_ROWS = 64;
 constexpr int MAX_TILE_BLOCKS = 512;
-constexpr int MAX_TILE_COLS = STG_THREADS / 2;  // one (column, half) per thread
+constexpr int PRODUCER_PAIRS = 4;       // (column, half) pairs per producer thread and item
+constexpr int MAX_TILE_COLS = PRODUCER_PAIRS * PRODUCER_THREADS / 2;
 constexpr int STG_SMEM_MAX = 232448;     // dynamic shared memory a CTA may use (227 KB)
 constexpr uint32_t STG_WAIT = 1u << 22;  // bounded polls of an mbarrier
 
@@ -84,7 +93,6 @@ __device__ __forceinline__ void cfma4(float2& acc, const float4& a01, const floa
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc05::smem_addr(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
@@ -109,119 +117,155 @@ struct PipeArgs {
     uint32_t off_meta, off_x, xq, stage_bytes;
 };
 
-// the column node this thread copies for item `item` (-1: none)
-__device__ __forceinline__ int item_col(const PipeArgs& a, int64_t item) {
-    if (item >= a.n_items) return -1;
-    const int tile = (int)(item / a.nrt);
-    const int c0 = a.tile_cptr[tile], nc = a.tile_cptr[tile + 1] - c0;
-    const int cl = threadIdx.x >> 1;
-    return cl < nc ? a.cols[c0 + cl] : -1;
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(tc05::smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc05::smem_addr(bar)) : "memory");
 }
 
-// stage `item` into `st`: bulk copies of blocks and metadata (thread 0) and the
-// x values of this thread's (column, half) for the item's right-hand sides
-__device__ __forceinline__ void stage_item(const PipeArgs& a, int64_t item, int node, unsigned char* st,
-                                           uint64_t* full) {
-    if (item >= a.n_items) return;
-    const int tile = (int)(item / a.nrt), r0 = (int)(item % a.nrt) * STG_KT;
-    const int kt = min(STG_KT, a.k - r0);
-    if (threadIdx.x == 0) {
-        const int row0 = a.tile_row[tile], row1 = a.tile_row[tile + 1];
-        const int blk0 = a.rp[row0], blk1 = a.rp[row1];
-        const int mo0 = a.meta_off[tile], mo1 = a.meta_off[tile + 1];
-        const uint32_t mbytes = (uint32_t)(blk1 - blk0) * 128u, tbytes = (uint32_t)(mo1 - mo0) * 16u;
-        tc05::mbar_expect_tx(full, mbytes + tbytes);
-        tc05::bulk_g2s(st, a.val + 16 * (int64_t)blk0, mbytes, full);
-        tc05::bulk_g2s(st + a.off_meta, a.meta + 16 * (int64_t)mo0, tbytes, full);
-    }
-    if (node >= 0) {
-        const int cl = threadIdx.x >> 1, h = threadIdx.x & 1;
-        unsigned char* dst = st + a.off_x + (uint32_t)cl * 32u + (uint32_t)h * 16u;
-        const float2* src = a.x + (int64_t)r0 * a.ldx + 4 * (int64_t)node + 2 * h;
-        for (int q = 0; q < kt; ++q) cp_async16(dst + (uint32_t)q * a.xq, src + (int64_t)q * a.ldx);
-    }
-}
-
+// Producer warps: for each item of this CTA, once its stage is free, thread 0
+// starts the bulk copies of the tile's blocks and metadata (expected bytes on
+// the stage's "full" mbarrier), and the producer threads copy x for every
+// (column, half) of the tile's list and every right-hand side with 16-byte
+// asynchronous copies whose completion also arrives on "full".  Consumer
+// warps wait on "full", compute one block row each and arrive on "empty".
+// No CTA-wide barrier: a warp that finishes its rows moves on to the next
+// staged item.
 template <int S>
 __global__ void __launch_bounds__(STG_THREADS, 1) k_spmm_pipe(const PipeArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + MAX_STAGES;
     unsigned char* base = smem + 128;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, p = lane & 3, q = lane >> 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) tc05::mbar_init(&full[s], 1);
+        for (int s = 0; s < S; ++s) {
+            tc05::mbar_init(&full[s], PRODUCER_THREADS + 1);
+            tc05::mbar_init(&empty[s], CONSUMER_WARPS);
+        }
         tc05::fence_barrier_init();
     }
     __syncthreads();
-    const int64_t G = gridDim.x, b0 = blockIdx.x;
-    // prologue: items 0 .. S-2 of this CTA into stages 0 .. S-2
-    for (int j = 0; j < S - 1; ++j) {
-        const int64_t item = b0 + j * G;
-        stage_item(a, item, item_col(a, item), base + (size_t)j * a.stage_bytes, &full[j]);
-        cp_async_commit();
-    }
-    int next_col = item_col(a, b0 + (S - 1) * G);
-    for (int64_t j = 0;; ++j) {
-        const int64_t item = b0 + j * G;
-        if (item >= a.n_items) break;
-        const int s = (int)(j % S);
-        __syncthreads();  // every warp is done with item j - 1: its stage takes item j + S - 1
-        {
-            const int64_t ahead = item + (S - 1) * G;
-            const int sa = (int)((j + S - 1) % S);
-            stage_item(a, ahead, next_col, base + (size_t)sa * a.stage_bytes, &full[sa]);
-            cp_async_commit();
-            next_col = item_col(a, ahead + G);
+    const int64_t G = gridDim.x;
+    if (warp < PRODUCER_WARPS) {
+        const int t = threadIdx.x;
+        int64_t j = 0;
+        for (int64_t item = blockIdx.x; item < a.n_items; item += G, ++j) {
+            const int tile = (int)(item / a.nrt), r0 = (int)(item % a.nrt) * STG_KT;
+            const int kt = min(STG_KT, a.k - r0);
+            // this thread's column nodes, loaded before the stage wait so the loads overlap it
+            const int c0 = a.tile_cptr[tile], nc = a.tile_cptr[tile + 1] - c0;
+            int node[PRODUCER_PAIRS];
+#pragma unroll
+            for (int m = 0; m < PRODUCER_PAIRS; ++m) {
+                const int e = t + m * PRODUCER_THREADS;
+                node[m] = e < 2 * nc ? a.cols[c0 + (e >> 1)] : -1;
+            }
+            const int s = (int)(j % S);
+            const uint32_t round = (uint32_t)(j / S);
+            if (round > 0 && !bwait(&empty[s], (round - 1) & 1u)) {
+                atomicOr(&g_staged_err, 1);
+                break;
+            }
+            unsigned char* st = base + (size_t)s * a.stage_bytes;
+            if (t == 0) {
+                const int row0 = a.tile_row[tile], row1 = a.tile_row[tile + 1];
+                const int blk0 = a.rp[row0], blk1 = a.rp[row1];
+                const int mo0 = a.meta_off[tile], mo1 = a.meta_off[tile + 1];
+                const uint32_t mbytes = (uint32_t)(blk1 - blk0) * 128u, tbytes = (uint32_t)(mo1 - mo0) * 16u;
+                tc05::mbar_expect_tx(&full[s], mbytes + tbytes);
+                tc05::bulk_g2s(st, a.val + 16 * (int64_t)blk0, mbytes, &full[s]);
+                tc05::bulk_g2s(st + a.off_meta, a.meta + 16 * (int64_t)mo0, tbytes, &full[s]);
+            }
+            unsigned char* xs = st + a.off_x;
+            const float2* xr = a.x + (int64_t)r0 * a.ldx;
+#pragma unroll
+            for (int m = 0; m < PRODUCER_PAIRS; ++m) {
+                if (node[m] < 0) continue;
+                const int e = t + m * PRODUCER_THREADS, cl = e >> 1, h = e & 1;
+                const float2* src = xr + 4 * (int64_t)node[m] + 2 * h;
+                unsigned char* dst = xs + (uint32_t)cl * 32u + (uint32_t)h * 16u;
+                for (int q = 0; q < kt; ++q) cp_async16(dst + (uint32_t)q * a.xq, src + (int64_t)q * a.ldx);
+            }
+            cp_async_arrive_noinc(&full[s]);  // arrives once this thread's copies have landed
         }
-        cp_async_wait<S - 1>();  // this thread's copies for item j have landed
-        __syncthreads();         // ... and everyone else's
+        cp_async_wait<0>();
+        return;
+    }
+    // ---- consumers: a warp takes 2 block rows at a time, 16 lanes per row, the two
+    // half-warps on alternate blocks of the row; lane (pp, qq) of a row computes
+    // scalar rows 2pp, 2pp + 1 for right-hand sides 2qq, 2qq + 1 (four complex
+    // accumulators), so each 16-byte shared-memory load feeds two outputs' worth
+    // of multiply-adds; the half-warps' partial sums meet in one shuffle
+    const int cw = warp - PRODUCER_WARPS, hh = lane >> 4, g = (lane >> 3) & 1, pp = (lane >> 2) & 1, qq = lane & 3;
+    const int p0 = 2 * pp, q0 = 2 * qq;
+    int64_t j = 0;
+    for (int64_t item = blockIdx.x; item < a.n_items; item += G, ++j) {
+        const int s = (int)(j % S);
         if (!bwait(&full[s], (uint32_t)(j / S) & 1u)) {
-            if (threadIdx.x == 0) atomicOr(&g_staged_err, 1);
-            cp_async_wait<0>();
+            if (lane == 0) atomicOr(&g_staged_err, 1);
             return;
         }
         const unsigned char* st = base + (size_t)s * a.stage_bytes;
-        const int tile = (int)(item / a.nrt), r0 = (int)(item % a.nrt) * STG_KT;
+        const int r0 = (int)(item % a.nrt) * STG_KT;
         const int kt = min(STG_KT, a.k - r0);
-        const bool store = q < kt && (!a.active || a.active[r0 + q]);
-        const int row0 = a.tile_row[tile], row1 = a.tile_row[tile + 1];
-        const int32_t* rps = reinterpret_cast<const int32_t*>(st + a.off_meta);
+        const bool st0 = q0 < kt && (!a.active || a.active[r0 + q0]);
+        const bool st1 = q0 + 1 < kt && (!a.active || a.active[r0 + q0 + 1]);
+        const int32_t* hdr = reinterpret_cast<const int32_t*>(st + a.off_meta);
+        const int row0 = hdr[0], row1 = hdr[1];  // from the staged metadata record
+        const int32_t* rps = hdr + 4;
         const uint16_t* lcs = reinterpret_cast<const uint16_t*>(rps + (row1 - row0 + 1));
-        const float4* ms4 = reinterpret_cast<const float4*>(st);
-        const unsigned char* xq = st + a.off_x + (uint32_t)q * a.xq;
-        for (int i = row0 + warp; i < row1; i += STG_WARPS) {
-            const int64_t e = (int64_t)(r0 + q) * a.ldy + 4 * (int64_t)i + p;
-            const float2 bv = (a.b && store) ? a.b[e] : make_float2(0.f, 0.f);  // in flight during the row
-            const int s0 = rps[i - row0], s1 = rps[i - row0 + 1];
-            float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
-            for (int sb = s0; sb < s1; sb += 32) {
-                const int n = min(32, s1 - sb);
-                const int lcv = lane < n ? (int)lcs[sb + lane] : 0;
-                const float4* mrow = ms4 + (int64_t)sb * 8 + 2 * p;
-                int jj = 0;
-                for (; jj + 1 < n; jj += 2) {
-                    const int l0 = __shfl_sync(0xffffffffu, lcv, jj);
-                    const int l1 = __shfl_sync(0xffffffffu, lcv, jj + 1);
-                    const float4* x0 = reinterpret_cast<const float4*>(xq + (uint32_t)l0 * 32u);
-                    const float4* x1 = reinterpret_cast<const float4*>(xq + (uint32_t)l1 * 32u);
-                    const float4 a01 = mrow[8 * jj], a23 = mrow[8 * jj + 1];
-                    const float4 b01 = mrow[8 * jj + 8], b23 = mrow[8 * jj + 9];
-                    const float4 u01 = x0[0], u23 = x0[1], v01 = x1[0], v23 = x1[1];
-                    cfma4(acc, a01, a23, u01, u23);
-                    cfma4(acc2, b01, b23, v01, v23);
-                }
-                if (jj < n) {
-                    const int l0 = __shfl_sync(0xffffffffu, lcv, jj);
-                    const float4* x0 = reinterpret_cast<const float4*>(xq + (uint32_t)l0 * 32u);
-                    cfma4(acc, mrow[8 * jj], mrow[8 * jj + 1], x0[0], x0[1]);
-                }
+        const unsigned char* mb = st + (uint32_t)pp * 64u;
+        const unsigned char* x0 = st + a.off_x + (uint32_t)q0 * a.xq;
+        const unsigned char* x1 = x0 + a.xq;
+        for (int i2 = row0 + 2 * cw; i2 < row1; i2 += 2 * CONSUMER_WARPS) {
+            const int i = i2 + g;
+            const bool row_ok = i < row1;
+            const int s0 = row_ok ? rps[i - row0] : 0, s1 = row_ok ? rps[i - row0 + 1] : 0;
+            const int64_t e0 = (int64_t)(r0 + q0) * a.ldy + 4 * (int64_t)i + p0;
+            const int64_t e1 = e0 + a.ldy;
+            float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;  // in flight during the row
+            if (a.b && row_ok && st0) b0 = *reinterpret_cast<const float4*>(a.b + e0);
+            if (a.b && row_ok && st1) b1 = *reinterpret_cast<const float4*>(a.b + e1);
+            float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;  // (row p0+., rhs q0+.)
+            for (int sb = s0 + hh; sb < s1; sb += 2) {  // the two half-warps take alternate blocks
+                const uint32_t lc = lcs[sb];
+                const float4* m = reinterpret_cast<const float4*>(mb + (uint32_t)sb * 128u);
+                const float4 m0a = m[0], m0b = m[1], m1a = m[2], m1b = m[3];  // rows p0, p0 + 1
+                const float4* u = reinterpret_cast<const float4*>(x0 + lc * 32u);
+                const float4* v = reinterpret_cast<const float4*>(x1 + lc * 32u);
+                const float4 ua = u[0], ub = u[1], va = v[0], vb = v[1];
+                cfma4(c00, m0a, m0b, ua, ub);
+                cfma4(c01, m0a, m0b, va, vb);
+                cfma4(c10, m1a, m1b, ua, ub);
+                cfma4(c11, m1a, m1b, va, vb);
             }
-            acc.x += acc2.x;
-            acc.y += acc2.y;
-            if (store) a.y[e] = a.b ? csub(bv, acc) : acc;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {  // add the other half-warp's partial sums (lane ^ 16)
+                float2* cc = o == 0 ? &c00 : &c01;
+                cc->x += __shfl_xor_sync(0xffffffffu, cc->x, 16);
+                cc->y += __shfl_xor_sync(0xffffffffu, cc->y, 16);
+            }
+            c10.x += __shfl_xor_sync(0xffffffffu, c10.x, 16);
+            c10.y += __shfl_xor_sync(0xffffffffu, c10.y, 16);
+            c11.x += __shfl_xor_sync(0xffffffffu, c11.x, 16);
+            c11.y += __shfl_xor_sync(0xffffffffu, c11.y, 16);
+            if (!row_ok || hh) continue;
+            if (st0) {
+                float4 o = make_float4(c00.x, c00.y, c10.x, c10.y);
+                if (a.b) o = make_float4(b0.x - o.x, b0.y - o.y, b0.z - o.z, b0.w - o.w);
+                *reinterpret_cast<float4*>(a.y + e0) = o;
+            }
+            if (st1) {
+                float4 o = make_float4(c01.x, c01.y, c11.x, c11.y);
+                if (a.b) o = make_float4(b1.x - o.x, b1.y - o.y, b1.z - o.z, b1.w - o.w);
+                *reinterpret_cast<float4*>(a.y + e1) = o;
+            }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
-    cp_async_wait<0>();  // nothing of this CTA's may still be in flight when it leaves
 }
 
 }  // namespace
@@ -283,13 +327,17 @@ void staged_plan_build(cudaStream_t st, StagedPlan& P, const std::vector<int32_t
         if (nc > MAX_TILE_COLS) return;
         blocks = rp[e] - rp[i];
         for (int u = 0; u < nc; ++u) loc[list[u]] = u;
-        // metadata record: row offsets (int32) then local columns (uint16), padded to 16 bytes
+        // metadata record: first and end row (int32, then 2 pad words), row offsets (int32),
+        // local columns (uint16), padded to 16 bytes
         const size_t m0 = meta.size();
         const int64_t nr = e - i;
-        const size_t bytes = (size_t)(nr + 1) * 4 + (size_t)blocks * 2;
+        const size_t bytes = 16 + (size_t)(nr + 1) * 4 + (size_t)blocks * 2;
         meta.resize(m0 + (bytes + 15) / 16 * 16, 0);
-        int32_t* ro = reinterpret_cast<int32_t*>(meta.data() + m0);
-        uint16_t* lc = reinterpret_cast<uint16_t*>(meta.data() + m0 + (size_t)(nr + 1) * 4);
+        int32_t* hd = reinterpret_cast<int32_t*>(meta.data() + m0);
+        hd[0] = (int32_t)i;
+        hd[1] = (int32_t)e;
+        int32_t* ro = hd + 4;
+        uint16_t* lc = reinterpret_cast<uint16_t*>(meta.data() + m0 + 16 + (size_t)(nr + 1) * 4);
         for (int64_t r = 0; r <= nr; ++r) ro[r] = rp[i + r] - rp[i];
         for (int32_t s = rp[i]; s < rp[e]; ++s) lc[s - rp[i]] = (uint16_t)loc[col[s]];
         tcols.insert(tcols.end(), list.begin(), list.end());

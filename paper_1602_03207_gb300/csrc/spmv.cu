@@ -292,7 +292,88 @@ __global__ void __launch_bounds__(256) k_spmv_df32(const int32_t* __restrict__ r
                 make_double2((double)sr[q] + (double)cr[q], (double)si[q] + (double)ci[q]);
 }
 
+// FP32 SpMM, one warp per block row, up to 8 right-hand sides per warp.
+// Lane (p, q) reads column p of each block (32 contiguous bytes of the
+// transposed copy; the four p lanes together read the block's 128 bytes and
+// the eight q lanes share them) and the value x_q[4c + p] (the 32 lanes read
+// the 8 vectors' 32-byte segments of column node c: one sector per vector),
+// and accumulates the four partial rows A[:, p] x_q[4c + p].  At the end of
+// the row the partials of the four p lanes are summed with shuffles and lane
+// (p, q) stores row p of y_q.  Against the thread-per-row kernel this halves
+// the L1 wavefronts per block (the x gather is one 8-sector request per block
+// instead of sixteen).
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_spmm_colwarp(const int32_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col, const float4* __restrict__ valt,
+                                                      const float2* __restrict__ x, int64_t ldx, const float2* b,
+                                                      float2* y, int64_t ldy, int64_t n_rows, int k,
+                                                      const int* __restrict__ active) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n_rows) return;  // uniform over the warp
+    const int lane = threadIdx.x & 31, p = lane & 3, q = lane >> 2;
+    const int r = blockIdx.y * 8 + q;
+    const bool live = r < k && (!active || active[r]);
+    if (!__any_sync(0xffffffffu, live)) return;
+    const float2* xq = x + (int64_t)min(r, k - 1) * ldx + p;  // lanes past k read the last vector, store nothing
+    float2 acc[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] = make_float2(0.f, 0.f);
+    const int s0 = row_ptr[i], s1 = row_ptr[i + 1];
+    for (int sb = s0; sb < s1; sb += 32) {
+        const int n = min(32, s1 - sb);
+        const int cv = lane < n ? col[sb + lane] : 0;
+        const float4* v = valt + (int64_t)sb * 8 + 2 * p;
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+            const int c0 = __shfl_sync(0xffffffffu, cv, j), c1 = __shfl_sync(0xffffffffu, cv, j + 1);
+            const float4 a01 = v[8 * j], a23 = v[8 * j + 1], b01 = v[8 * j + 8], b23 = v[8 * j + 9];
+            const float2 x0 = xq[4 * (int64_t)c0], x1 = xq[4 * (int64_t)c1];
+            cfma(acc[0], make_float2(a01.x, a01.y), x0);
+            cfma(acc[1], make_float2(a01.z, a01.w), x0);
+            cfma(acc[2], make_float2(a23.x, a23.y), x0);
+            cfma(acc[3], make_float2(a23.z, a23.w), x0);
+            cfma(acc[0], make_float2(b01.x, b01.y), x1);
+            cfma(acc[1], make_float2(b01.z, b01.w), x1);
+            cfma(acc[2], make_float2(b23.x, b23.y), x1);
+            cfma(acc[3], make_float2(b23.z, b23.w), x1);
+        }
+        if (j < n) {
+            const int c0 = __shfl_sync(0xffffffffu, cv, j);
+            const float4 a01 = v[8 * j], a23 = v[8 * j + 1];
+            const float2 x0 = xq[4 * (int64_t)c0];
+            cfma(acc[0], make_float2(a01.x, a01.y), x0);
+            cfma(acc[1], make_float2(a01.z, a01.w), x0);
+            cfma(acc[2], make_float2(a23.x, a23.y), x0);
+            cfma(acc[3], make_float2(a23.z, a23.w), x0);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            acc[e].x += __shfl_xor_sync(0xffffffffu, acc[e].x, o);
+            acc[e].y += __shfl_xor_sync(0xffffffffu, acc[e].y, o);
+        }
+    if (!live) return;
+    const float2 mine = p == 0 ? acc[0] : p == 1 ? acc[1] : p == 2 ? acc[2] : acc[3];
+    const int64_t e = (int64_t)r * ldy + 4 * i + p;
+    y[e] = RESID ? csub(b[e], mine) : mine;
+}
+
 }  // namespace
+
+void bsr_spmm_colwarp_f32(cudaStream_t st, const int32_t* rp, const int32_t* col, const float2* valt, int64_t N,
+                          const float2* x, int64_t ldx, const float2* b, float2* y, int64_t ldy, int k,
+                          const int* active) {
+    const dim3 grid(grid_for(32 * N, 256), (unsigned)((k + 7) / 8));
+    if (b)
+        k_spmm_colwarp<true><<<grid, 256, 0, st>>>(rp, col, reinterpret_cast<const float4*>(valt), x, ldx, b, y, ldy,
+                                                   N, k, active);
+    else
+        k_spmm_colwarp<false><<<grid, 256, 0, st>>>(rp, col, reinterpret_cast<const float4*>(valt), x, ldx, b, y,
+                                                    ldy, N, k, active);
+    ECT_CHECK_LAUNCH();
+}
 
 void bsr_spmv_f64(cudaStream_t st, const int32_t* rp, const int32_t* cl, const double2* val, int64_t N,
                   const double2* x, const double2* b, double2* y, int k, int64_t ldx, int rhs_tile, const int* active) {
@@ -359,6 +440,11 @@ void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t 
               const int* active) {
     Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.assembled && M.has_f32, ECT_ERR_STATE, "FP32 matrix not assembled (use ECT_F32 in ect_assemble)");
+    if (c->staged_rows == SPMM_COLWARP && rhs_tile != -1) {
+        bsr_spmm_colwarp_f32(c->stream, c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), M.sval32t.as<float2>(),
+                             c->n_nodes, x, ldx, nullptr, y, ldx, k, active);
+        return;
+    }
     if (c->staged_rows > 0 && rhs_tile != -1 && c->fine_plan.ok && c->fine_plan.rows == c->staged_rows) {
         bsr_spmm_staged_f32(c->stream, c->fine_plan, c->row_ptr.as<int32_t>(), M.sval32.as<float2>(), x, ldx,
                             nullptr, y, ldx, k, active);

@@ -38,7 +38,7 @@ _NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_CUDA", 4: "ERR_OOM", 5: 
 EXPORTS = ["ect_default_options", "ect_create", "ect_destroy", "ect_last_error", "ect_set_mesh",
            "ect_set_physics", "ect_assemble", "ect_precond_setup", "ect_matrix_info", "ect_matrix_copy",
            "ect_scaling_copy", "ect_spmv", "ect_precond_apply", "ect_cgs2", "ect_coil_rhs", "ect_solve",
-           "ect_delta_z", "ect_impedance", "ect_autotune", "ect_set_defect", "ect_delta_z_static", "ect_set_spmm_rows", "ect_partition", "ect_set_ibc", "ect_assemble_sweep", "ect_solve_sweep",
+           "ect_delta_z", "ect_impedance", "ect_autotune", "ect_set_defect", "ect_delta_z_static", "ect_set_spmm_rows", "ect_partition", "ect_set_ibc", "ect_assemble_sweep", "ect_solve_sweep", "ect_set_block_split", "ect_get_block_split",
            "ect_impedance_sweep", "ect_mlp_num_params", "ect_mlp_create",
            "ect_mlp_destroy", "ect_mlp_last_error", "ect_mlp_set_params", "ect_mlp_get_params", "ect_mlp_forward",
            "ect_mlp_gradients", "ect_mlp_train_step"]
@@ -104,6 +104,8 @@ def load_library(path=LIB_PATH):
         "ect_partition": (I, [P, I64, I, P, P]),
         "ect_set_ibc": (I, [P, I, P, D, D]),
         "ect_assemble_sweep": (I, [P, P, I, I]),
+        "ect_set_block_split": (I, [P, I]),
+        "ect_get_block_split": (I, [P]),
         "ect_solve_sweep": (I, [P, I, P, P, I, ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
         "ect_impedance_sweep": (I, [P, ctypes.POINTER(Coil), P, I, ctypes.POINTER(Options), P, ctypes.POINTER(Stats)]),
         "ect_cgs2": (I, [P, I, P, I, I64, P, P, P]),
@@ -279,6 +281,12 @@ class Context:
     # ---- kernels -------------------------------------------------------------
     def spmv(self, which, x, y, k=1, precision=ECT_F64):
         self._call(self.L.ect_spmv, int(which), int(precision), _dptr(x), _dptr(y), int(k))
+
+    def set_block_split(self, parts):
+        self._call(self.L.ect_set_block_split, int(parts))
+
+    def block_split(self):
+        return int(self.L.ect_get_block_split(self.h))
 
     def set_spmm_rows(self, rows):
         self._call(self.L.ect_set_spmm_rows, int(rows))

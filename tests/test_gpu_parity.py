@@ -132,7 +132,7 @@ def test_spmv_f64_batch(ect, small):
         assert np.abs(Y - ref).max() <= 1e-13 * scale, k
 
 
-@pytest.mark.parametrize("rows", [0, 8, 64, -1])          # staged tilings (auto = 32) and the unstaged kernel
+@pytest.mark.parametrize("rows", [0, 8, 64, -1, -2])      # staged tilings (auto = 16), thread- and warp-per-row
 def test_spmv_f32_scaled(ect, small, rows):
     p, ctx, M = small
     rng = np.random.default_rng(1)
@@ -162,7 +162,7 @@ def test_spmv_f32_staged_many_tiles(ect):
     rng = np.random.default_rng(7)
     X = crand(rng, 9, S.shape[0]).astype(np.complex64)
     ref = (S @ X.T.astype(np.complex128)).T
-    for rows in (16, 0):
+    for rows in (16, 0, -2):
         ctx.set_spmm_rows(rows)
         x = dev(X, torch.complex64)
         y = torch.empty_like(x)
@@ -216,7 +216,7 @@ def test_multigrid_apply_matches_oracle(ect, prec, shape):
     refs = [solve.amg_apply(lv, R[q]) for q in range(k)]
     dt, pr, tol = ((torch.complex128, ect.ECT_F64, 1e-7) if prec == "f64" else (torch.complex64, ect.ECT_F32, 1e-2))
     r = dev(R, dt)
-    for rows in ((0, -1) if prec == "f32" else (0,)):
+    for rows in ((0, -1, -2) if prec == "f32" else (0,)):
         ctx.set_spmm_rows(rows)
         z = torch.empty_like(r)
         ctx.precond_apply(1, r, z, k, precision=pr)
@@ -324,7 +324,7 @@ def test_solve_residual_with_oracle_matrix(ect, small, mode, graph):
         assert st["converged"] == 2
 
 
-@pytest.mark.parametrize("rows", [8, 16, -1])
+@pytest.mark.parametrize("rows", [8, 16, -1, -2])
 def test_mixed_solve_spmm_tilings(ect, small, rows):
     """Mixed mode with the staged FP32 SpMM at other row tilings and with the unstaged kernels."""
     p, ctx, M = small

@@ -185,6 +185,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
+    if args.block_split:
+        ctx.set_block_split(args.block_split)
     asm_ms = [timed(lambda w=w: ctx.assemble(w, mask)) for w in (0, 1)]
     pc_ms = [timed(lambda w=w: ctx.precond_setup(w, mask)) for w in (0, 1)]
     _, nnzb = ctx.matrix_info()
@@ -219,7 +221,8 @@ def run_gpu(args):
             ms_pair = ctx.solve(0, Bsrc, U0, k, o)["ms"] + ctx.solve(1, Bsrc, Ud, k, o)["ms"]
             if best_ms is None or ms_pair < best_ms:
                 mixed, best_ms = o, ms_pair
-        tune = {"rhs_tile": mixed.rhs_tile, "spmm_rows": mixed.spmm_rows, "restart": mixed.restart,
+        tune = {"rhs_tile": mixed.rhs_tile, "spmm_rows": mixed.spmm_rows, "block_split": ctx.block_split(),
+                "restart": mixed.restart,
                 "inner_iters": mixed.inner_iters,
                 "reorth": mixed.reorth, "seconds": time.time() - t_at, "pair_ms": best_ms,
                 "tuned_on": "vacuum and defect systems; the faster option set on both"}
@@ -334,6 +337,7 @@ def run_gpu(args):
                    "positions_per_step": P * world, "rhs_per_solve_call": k, "nnzb": nnzb,
                    "inner_iters": mixed.inner_iters, "outer_restart": mixed.restart,
                    "reorth": mixed.reorth, "rhs_tile": mixed.rhs_tile, "spmm_rows": mixed.spmm_rows,
+                   "block_split": ctx.block_split(),
                    "l2": "inputs larger than L2 (matrices 3.8 GB FP64 / 1.9 GB FP32 each)",
                    "parallelism": f"positions sharded over {world} GPU(s)"},
         "clocks": clocks,
@@ -641,6 +645,8 @@ def main():
     ap.add_argument("--max-outer", type=int, default=400)
     ap.add_argument("--inner-iters", type=int, default=20)
     ap.add_argument("--reorth", type=int, default=1, help="Gram-Schmidt variant when not autotuned (0-3)")
+    ap.add_argument("--block-split", type=int, default=0,
+                    help="smoothing blocks per subdomain when not autotuned (0: the library's default, 1)")
     ap.add_argument("--spmm-rows", type=int, default=0,
                     help="FP32 SpMM row tiling when not autotuned (0 auto, -1 unstaged)")
     ap.add_argument("--no-autotune", action="store_true")

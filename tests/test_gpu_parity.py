@@ -472,8 +472,11 @@ def test_autotune_returns_converging_options(ect, small):
         best, st = ctx.autotune(1, b, work, 2, ect.default_options(tol=1e-10, mode=mode))
         assert best.rhs_tile in (-1, 1, 2, 4, 8) and st["converged"] == 2
         assert best.mode == mode and 1 <= best.restart <= 64
-        X, st2 = _solve_check(ect, p, ctx, M, "defect", best)
-        assert st2["converged"] == 2
+        assert best.spmm_rows in ((0, 24, 16, -1, -2) if mode == ect.ECT_MODE_MIXED else (0,))
+        assert ctx.block_split() in (1, 2)                 # the subdomain split the tuner applied
+        for w in ("defect", "vacuum"):                     # both preconditioners rebuilt for it
+            X, st2 = _solve_check(ect, p, ctx, M, w, best)
+            assert st2["converged"] == 2
 
 
 def test_set_defect_reassembles_only_the_defect_matrix(ect):

@@ -623,7 +623,16 @@ def mlp_probe(args):
     s_ms = timed(lambda: net.train_step(x, t, 1e-4), 10)
     peaks, src = load_peaks()
     pk = float(peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"]))
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    # algorithmic bytes of the inference forward: per layer the bf16 input once (the first layer's
+    # padded to 16 columns), the bf16 activations written once (the output layer: fp32), the bf16
+    # weights once; x read and y copied out at the ends
+    fwd_bytes = bt * sizes[0] * 4 + 2 * bt * sizes[-1] * 4
+    for l, (fi, fo) in enumerate(zip(sizes[:-1], sizes[1:])):
+        fwd_bytes += bt * (16 if l == 0 else fi) * 2 + bt * fo * (4 if l == len(sizes) - 2 else 2) + fo * fi * 2
     rec = {"mlp_probe": "ok", "batch": bt, "forward_ms": f_ms, "forward_tflops": fwd_flop / f_ms / 1e9,
+           "forward_bytes": fwd_bytes, "forward_gbs": fwd_bytes / f_ms / 1e6,
+           "forward_hbm_frac": fwd_bytes / f_ms / 1e6 / hbm,
            "train_step_ms": s_ms, "train_step_tflops": 3 * fwd_flop / s_ms / 1e9,
            "bf16_peak_tflops": pk, "peak_source": src,
            "forward_frac": fwd_flop / f_ms / 1e9 / pk, "train_step_frac": 3 * fwd_flop / s_ms / 1e9 / pk}

@@ -80,6 +80,11 @@ typedef struct {
     int spmm_rows;      /* FP32 SpMM variant: > 0 block rows per shared-memory-staged tile;
                            0 = auto (32); -1 = one thread per scalar row (x gathered from
                            L1/L2); -2 = one warp per block row over the transposed blocks */
+    int x0;             /* ect_solve / ect_solve_sweep: 1 = d_x holds an initial guess (for
+                           example the background solution when solving the defect
+                           configuration), 0 = start from zero (d_x need not be initialised).
+                           The tolerance stays relative to ||T b||.  Ignored by the calls that
+                           own their solution buffers (impedance, autotune). */
 } ect_options;
 
 typedef struct {
@@ -95,7 +100,8 @@ typedef struct {
 
 /* Fill *opt with defaults: tol 1e-10, restart 30, max_iters 20000, F64 mode,
  * inner_iters 30, graphs on, automatic rhs tile, no timeout, selective
- * reorthogonalisation, staged FP32 SpMM with automatic row tiling. */
+ * reorthogonalisation, staged FP32 SpMM with automatic row tiling, zero
+ * initial guess. */
 void ect_default_options(ect_options* opt);
 
 /* Create a context bound to a CUDA stream (a cudaStream_t, may be NULL for the
@@ -244,7 +250,8 @@ int ect_coil_rhs(ect_ctx* ctx, const ect_coil* coil, const double* h_z_probe, in
 
 /* Step 5-6: solve M x = b for k right-hand sides of configuration `which`
  * with preconditioned flexible GMRES (or the mixed FP64/FP32 scheme).
- * d_rhs, d_x complex128 [k][n_nodes][4]; d_x need not be initialised.
+ * d_rhs, d_x complex128 [k][n_nodes][4]; d_x need not be initialised unless
+ * opt->x0 = 1, in which case it holds the initial guess.
  * Needs ect_assemble and ect_precond_setup (with ECT_F32 for mixed mode). */
 int ect_solve(ect_ctx* ctx, int which, const void* d_rhs, void* d_x, int k,
               const ect_options* opt, ect_stats* stats);

@@ -51,6 +51,7 @@ void ect_default_options(ect_options* o) {
     o->timeout_s = 0.0;
     o->reorth = 1;
     o->spmm_rows = 0;
+    o->x0 = 0;
 }
 
 int ect_create(ect_ctx** out, void* stream) {
@@ -258,6 +259,7 @@ int ect_autotune(ect_ctx* c, int which, const void* d_rhs, void* d_work, int k, 
         ect_options o;
         if (base) o = *base;
         else ect_default_options(&o);
+        o.x0 = 0;  // the solution buffers are this call's own
         Matrix& M = ctx_mat(c, which);
         ECT_REQUIRE(M.assembled && M.pc_f64, ECT_ERR_STATE, "assemble and set up the preconditioner first");
         const bool mixed = o.mode == ECT_MODE_MIXED;
@@ -447,6 +449,7 @@ int ect_impedance_sweep(ect_ctx* c, const ect_coil coils[2], const double* h_z_p
         ect_options o;
         if (opt) o = *opt;
         else ect_default_options(&o);
+        o.x0 = 0;  // the solution buffers are this call's own
         const int64_t nvec = 4 * c->n_nodes;
         size_t fr = 0, tot = 0;
         ECT_CUDA(cudaMemGetInfo(&fr, &tot));
@@ -525,6 +528,7 @@ int ect_impedance(ect_ctx* c, const ect_coil coils[2], const double* h_z_pos, in
         ect_options o;
         if (opt) o = *opt;
         else ect_default_options(&o);
+        o.x0 = 0;  // the solution buffers are this call's own
         const int64_t nvec = 4 * c->n_nodes;
         // positions per batch: bounded by the Krylov workspace of 2 rhs per position
         size_t fr = 0, tot = 0;

@@ -421,7 +421,8 @@ void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, cons
 // and poff are the packed FP32 inverses and their offsets
 template <typename T>
 void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, const C<T>* pinv, int64_t n_blocks,
-                 const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate);
+                 int max_block_nodes, const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active,
+                 bool accumulate);
 void dense_inverse(cudaStream_t st, double2* a, int64_t n);
 void to_f32(cudaStream_t st, const double2* a, float2* b, int64_t n);
 int64_t gemv_scratch_elems(int64_t nc, int k);

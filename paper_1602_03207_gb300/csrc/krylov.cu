@@ -494,6 +494,17 @@ __global__ void k_diag_scale(const double2* __restrict__ in, double2* __restrict
         out[(int64_t)r * ld + e] = cscale(in[(int64_t)r * ld + e], t[e]);
 }
 
+// out = in / t elementwise (t > 0: the scaling of the system)
+__global__ void k_diag_unscale(const double2* __restrict__ in, double2* __restrict__ out, const double* __restrict__ t,
+                               int64_t ld, int64_t n) {
+    const int r = blockIdx.y;
+    for (int64_t e = blockIdx.x * (int64_t)TPB + threadIdx.x; e < n; e += (int64_t)gridDim.x * TPB) {
+        const double2 v = in[(int64_t)r * ld + e];
+        const double it = 1.0 / t[e];
+        out[(int64_t)r * ld + e] = make_double2(v.x * it, v.y * it);
+    }
+}
+
 template <typename T>
 __global__ void k_zero(C<T>* __restrict__ a, int64_t ld, int64_t n, const int* __restrict__ live) {
     const int r = blockIdx.y;
@@ -803,19 +814,34 @@ void solve_groups(ect_ctx* c, const Groups& G, const double2* rhs, double2* x, i
     for (const Group& g : G)
         k_diag_scale<<<dim3(ew_blocks(n, g.k), g.k), TPB, 0, st>>>(rhs + g.rhs_r0 * ld, w->Bh.as<double2>() + g.r0 * ld,
                                                                   ctx_mat(c, g.which).t.as<double>(), ld, n);
-    ECT_CUDA(cudaMemsetAsync(w->Y.p, 0, sizeof(double2) * n * k, st));
-    ECT_CUDA(cudaMemcpyAsync(w->R.p, w->Bh.p, sizeof(double2) * n * k, cudaMemcpyDeviceToDevice, st));
     k_norm_part<double><<<vgrid(w), TPB, 0, st>>>(w->Bh.as<double2>(), ld, n, nullptr, w->npart.as<double>(), w->G);
     k_norm_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(w->npart.as<double>(), w->G, k, nullptr, w->bnorm.as<double>());
-    ECT_CUDA(cudaMemcpyAsync(w->rnorm.p, w->bnorm.p, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+    if (opt.x0) {
+        // Y = T^-1 x0, R = Bh - S Y and its norm
+        for (const Group& g : G)
+            k_diag_unscale<<<dim3(ew_blocks(n, g.k), g.k), TPB, 0, st>>>(x + g.r0 * ld, w->Y.as<double2>() + g.r0 * ld,
+                                                                        ctx_mat(c, g.which).t.as<double>(), ld, n);
+        const std::vector<int> all(k, 1);
+        ECT_CUDA(cudaMemcpyAsync(w->run.p, all.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+        g_spmv_f64(c, G, w->Y.as<double2>(), w->R.as<double2>(), ld, opt.rhs_tile, w->run.as<int>());
+        k_residual<<<vgrid(w), TPB, 0, st>>>(w->Bh.as<double2>(), w->R.as<double2>(), ld, n, w->run.as<int>(),
+                                            w->npart.as<double>(), w->G);
+        k_norm_finalize<<<grid_for((int64_t)k * 32, 128), 128, 0, st>>>(w->npart.as<double>(), w->G, k,
+                                                                        w->run.as<int>(), w->rnorm.as<double>());
+        ECT_CHECK_LAUNCH();
+    } else {
+        ECT_CUDA(cudaMemsetAsync(w->Y.p, 0, sizeof(double2) * n * k, st));
+        ECT_CUDA(cudaMemcpyAsync(w->R.p, w->Bh.p, sizeof(double2) * n * k, cudaMemcpyDeviceToDevice, st));
+        ECT_CUDA(cudaMemcpyAsync(w->rnorm.p, w->bnorm.p, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+    }
     ECT_CUDA(cudaMemsetAsync(w->flags.p, 0, sizeof(int), st));
     std::vector<double> bnorm(k), rnorm(k), target(k), target_i(k, 0.0);
     ECT_CUDA(cudaMemcpyAsync(bnorm.data(), w->bnorm.p, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    ECT_CUDA(cudaMemcpyAsync(rnorm.data(), w->rnorm.p, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
     ECT_CUDA(cudaStreamSynchronize(st));
     for (int r = 0; r < k; ++r) target[r] = opt.tol * bnorm[r];
     ECT_CUDA(cudaMemcpyAsync(w->target.p, target.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
     if (mi) ECT_CUDA(cudaMemcpyAsync(w->target_i.p, target_i.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-    rnorm = bnorm;
     std::vector<int> run(k), nit(k), iters(k, 0), outer(k, 0);
     const bool graphs = opt.use_graph && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     auto t_start = std::chrono::steady_clock::now();

@@ -10,6 +10,7 @@
 // bias gradients, and Adam, which also rewrites the bf16 weight copies.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -61,12 +62,25 @@ __global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict
     }
 }
 
-// db[n] = sum_b dz[b][n] (fixed order)
-__global__ void k_bias_grad(const float* __restrict__ dz, int B, int N, float* __restrict__ db) {
+// bias gradient, two passes in a fixed order: part[y][n] = sum over the rows of chunk y of
+// dz[b][n], then db[n] = sum over y of part[y][n]
+constexpr int BIAS_CHUNKS = 64;
+
+__global__ void k_bias_grad_part(const float* __restrict__ dz, int B, int N, float* __restrict__ part) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int rows = (B + BIAS_CHUNKS - 1) / BIAS_CHUNKS;
+    const int b0 = blockIdx.y * rows, b1 = min(B, b0 + rows);
+    float s = 0.0f;
+    for (int b = b0; b < b1; ++b) s += dz[(int64_t)b * N + n];
+    part[(int64_t)blockIdx.y * N + n] = s;
+}
+
+__global__ void k_bias_grad_sum(const float* __restrict__ part, int N, float* __restrict__ db) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     float s = 0.0f;
-    for (int b = 0; b < B; ++b) s += dz[(int64_t)b * N + n];
+    for (int y = 0; y < BIAS_CHUNKS; ++y) s += part[(int64_t)y * N + n];
     db[n] = s;
 }
 
@@ -116,6 +130,9 @@ struct ect_mlp {
     DevBuf dZf, dZc, dZTc;        // current dz (fp32, canonical, transposed canonical)
     DevBuf dZf2, dZc2, dZTc2;     // ping-pong
     DevBuf lpart, errflag;
+    DevBuf part;                  // split-K partial products of the weight-gradient GEMMs
+    DevBuf bpart;                 // bias-gradient partial sums
+    int n_sms = 0;
     int t = 0;
 };
 
@@ -125,18 +142,64 @@ int64_t n_params_of(int l) { return (int64_t)kOut[l] * kIn[l] + kOut[l]; }
 
 void gemm(ect_mlp* m, const uint8_t* A, const uint8_t* Bm, int M, int N, int K, int mode, const float* bias,
           const float* zprev, float* Zf, float* Yf, uint8_t* Xc, uint8_t* XTc) {
-    ECT_REQUIRE(M % 128 == 0 && N % 16 == 0 && N >= 16 && N <= 256 && K % 16 == 0 &&
-                    (K <= mlpk::KC || K % mlpk::KC == 0),
+    using namespace mlpk;
+    ECT_REQUIRE(M % 128 == 0 && M > 0 && N % 16 == 0 && N >= 16 && N <= 256 && K % 16 == 0 && K >= 16 &&
+                    (K <= KCH_MAX || K % KCH_MAX == 0),
                 ECT_ERR_ARG, "unsupported GEMM shape");
-    mlpk::GemmArgs g{A, Bm, M, N, K, mode, bias, zprev, Zf, Yf, Xc, XTc, m->errflag.as<int>()};
-    const int kc = K < mlpk::KC ? K : mlpk::KC;
-    const size_t smem = (size_t)(128 + N) * kc * 2;
-    ECT_CUDA(cudaFuncSetAttribute(mlpk::k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    mlpk::k_gemm_tc<<<M / 128, 128, smem, m->stream>>>(g);
+    GemmArgs g{};
+    g.A = A;
+    g.B = Bm;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.mode = mode;
+    g.bias = bias;
+    g.zprev = zprev;
+    g.Zf = Zf;
+    g.Yf = Yf;
+    g.Xc = Xc;
+    g.XTc = XTc;
+    g.err = m->errflag.as<int>();
+    g.kch = K < KCH_MAX ? K : KCH_MAX;
+    const int nch = K / g.kch, mtiles = M / 128;
+    g.resident = (mode != BWD_DW && (uint32_t)N * K * 2 <= RESIDENT_B_MAX) ? 1 : 0;
+    ECT_REQUIRE(g.resident || mode == BWD_DW, ECT_ERR_ARG, "weights too large for the resident-B GEMM");
+    g.nsplit = 1;
+    g.ksplit = nch;
+    if (mode == BWD_DW) {  // K (the batch) split so that the items fill the SMs
+        const int want = std::max(1, std::min(nch, m->n_sms / mtiles));
+        g.ksplit = (nch + want - 1) / want;
+        g.nsplit = (nch + g.ksplit - 1) / g.ksplit;
+    }
+    g.a_bytes = 128u * (uint32_t)g.kch * 2u;
+    g.stage_tx = g.a_bytes + (g.resident ? 0u : (uint32_t)N * g.kch * 2u);
+    g.stage_bytes = (g.stage_tx + 1023u) / 1024u * 1024u;
+    g.b_tx = g.resident ? (uint32_t)N * K * 2u : 0u;
+    g.b_bytes = (g.b_tx + 1023u) / 1024u * 1024u;
+    const int room = PIPE_SMEM_MAX - (int)g.b_bytes - EPI_BYTES;
+    g.stages = std::min(PIPE_MAX_STAGES, room / (int)g.stage_bytes);
+    ECT_REQUIRE(g.stages >= 2, ECT_ERR_ARG, "GEMM stages do not fit in shared memory (internal)");
+    if (g.nsplit > 1) {
+        const size_t need = sizeof(float) * (size_t)g.nsplit * M * N;
+        if (m->part.bytes < need) m->part.alloc(need);
+        g.part = m->part.as<float>();
+    }
+    const size_t smem = (size_t)g.b_bytes + (size_t)g.stages * g.stage_bytes + EPI_BYTES;
+    ECT_CUDA(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int items = mtiles * g.nsplit;
+    const int grid = std::min(items, m->n_sms);
+    k_gemm_tc<<<grid, PIPE_THREADS, smem, m->stream>>>(g);
     ECT_CHECK_LAUNCH();
+    if (g.nsplit > 1) {
+        const int64_t n4 = (int64_t)M * N / 4;
+        k_sum_splits<<<grid_for(n4, 256), 256, 0, m->stream>>>(reinterpret_cast<const float4*>(g.part), g.nsplit, n4,
+                                                             reinterpret_cast<float4*>(Yf));
+        ECT_CHECK_LAUNCH();
+    }
 }
 
-void forward(ect_mlp* m, const float* d_x) {
+// train: keep what the backward pass reads (pre-activations, transposed activations)
+void forward(ect_mlp* m, const float* d_x, bool train) {
     const int B = m->B;
     cudaStream_t st = m->stream;
     k_pack_input<<<grid_for(B, 128), 128, 0, st>>>(d_x, B, m->Xc[0].as<uint8_t>(), m->XTc[0].as<uint8_t>());
@@ -145,8 +208,9 @@ void forward(ect_mlp* m, const float* d_x) {
     for (int l = 0; l < NL; ++l) {
         const float* bias = P + m->off[l] + (int64_t)kOut[l] * kIn[l];
         if (l < NL - 1)
-            gemm(m, m->Xc[l].as<uint8_t>(), m->Wc[l].as<uint8_t>(), B, kOut[l], kInPad[l], mlpk::FWD_HIDDEN, bias,
-                 nullptr, m->Zf[l].as<float>(), nullptr, m->Xc[l + 1].as<uint8_t>(), m->XTc[l + 1].as<uint8_t>());
+            gemm(m, m->Xc[l].as<uint8_t>(), m->Wc[l].as<uint8_t>(), B, kOut[l], kInPad[l],
+                 train ? mlpk::FWD_HIDDEN : mlpk::FWD_INFER, bias, nullptr, m->Zf[l].as<float>(), nullptr,
+                 m->Xc[l + 1].as<uint8_t>(), m->XTc[l + 1].as<uint8_t>());
         else
             gemm(m, m->Xc[l].as<uint8_t>(), m->Wc[l].as<uint8_t>(), B, kOut[l], kInPad[l], mlpk::FWD_OUT, bias,
                  nullptr, nullptr, m->Y.as<float>(), nullptr, nullptr);
@@ -157,7 +221,7 @@ void forward(ect_mlp* m, const float* d_x) {
 int backward(ect_mlp* m, const float* d_x, const float* d_t) {
     const int B = m->B;
     cudaStream_t st = m->stream;
-    forward(m, d_x);
+    forward(m, d_x, true);
     const int64_t nout = (int64_t)B * OUT;
     const int lb = (int)grid_for(nout, 256);
     k_loss_grad<<<lb, 256, 0, st>>>(m->Y.as<float>(), d_t, B, OUT, m->dZf.as<float>(), m->dZc.as<uint8_t>(),
@@ -180,7 +244,10 @@ int backward(ect_mlp* m, const float* d_x, const float* d_t) {
             ECT_CUDA(cudaMemcpy2DAsync(gW, sizeof(float) * kIn[l], m->Y.p, sizeof(float) * kInPad[l],
                                        sizeof(float) * kIn[l], kOut[l], cudaMemcpyDeviceToDevice, st));
         }
-        k_bias_grad<<<grid_for(kOut[l], 128), 128, 0, st>>>(cur[0]->as<float>(), B, kOut[l], gb);
+        k_bias_grad_part<<<dim3((unsigned)grid_for(kOut[l], 128), BIAS_CHUNKS), 128, 0, st>>>(
+            cur[0]->as<float>(), B, kOut[l], m->bpart.as<float>());
+        ECT_CHECK_LAUNCH();
+        k_bias_grad_sum<<<grid_for(kOut[l], 128), 128, 0, st>>>(m->bpart.as<float>(), kOut[l], gb);
         ECT_CHECK_LAUNCH();
         if (l > 0) {
             // dX (B x in) = dZ (B x out) * W (out x in) -> dz_{l-1} = dX * silu'(Z_{l-1})
@@ -271,6 +338,10 @@ int ect_mlp_create(ect_mlp** out, void* stream, int batch) {
             for (DevBuf* b : {&m->dZc, &m->dZTc, &m->dZc2, &m->dZTc2}) b->alloc((size_t)2 * batch * H);
             m->lpart.alloc(sizeof(double) * grid_for((int64_t)batch * OUT, 256));
             m->errflag.alloc(sizeof(int));
+            m->bpart.alloc(sizeof(float) * BIAS_CHUNKS * std::max(H, OUT));
+            int dev = 0;
+            ECT_CUDA(cudaGetDevice(&dev));
+            ECT_CUDA(cudaDeviceGetAttribute(&m->n_sms, cudaDevAttrMultiProcessorCount, dev));
             ECT_CUDA(cudaMemsetAsync(m->errflag.p, 0, sizeof(int), m->stream));
             ECT_CUDA(cudaStreamSynchronize(m->stream));
         } catch (...) {
@@ -323,7 +394,7 @@ int ect_mlp_forward(ect_mlp* m, const float* d_x, float* d_y) {
     if (!m) return ECT_ERR_ARG;
     return mguard(m, [&] {
         ECT_REQUIRE(d_x && d_y, ECT_ERR_ARG, "null x or y");
-        forward(m, d_x);
+        forward(m, d_x, false);
         ECT_CUDA(cudaMemcpyAsync(d_y, m->Y.p, sizeof(float) * (size_t)m->B * OUT, cudaMemcpyDeviceToDevice,
                                  m->stream));
         check_err(m);

@@ -629,7 +629,8 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
     C<T>* t = (C<T>*)L.t.p;
     const C<T>* val = lvl_val<T>(L);
     const T* w = lvl_w<T>(L);
-    block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, r, z, k, ld, tile, active, false);
+    block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, L.max_agg, r, z, k, ld, tile, active,
+                   false);
     const int gamma = last ? 1 : 2;
     // t = r - A z: one thread per scalar row, or one warp per block row on the small coarse
     // levels (few rows, many blocks per row: the warp splits the row's serial chain of loads)
@@ -670,7 +671,8 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
         }
     }
     if (!L.has_ap) residual();
-    block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, t, z, k, ld, tile, active, true);
+    block_apply<T>(st, L.d_agg_ptr, lvl_poff<T>(L), lvl_pinv<T>(L), L.n_agg, L.max_agg, t, z, k, ld, tile, active,
+                   true);
     ECT_CHECK_LAUNCH();
 }
 

@@ -301,14 +301,18 @@ __global__ void __launch_bounds__(64) k_block_apply_sym8x2(const int32_t* __rest
                                                           const int* __restrict__ active,
                                                           const int32_t* __restrict__ blk_c,
                                                           const float2* __restrict__ zc, int64_t nc,
-                                                          const float* __restrict__ zv, int accumulate, int ntile) {
+                                                          const float* __restrict__ zv, int accumulate, int ntile,
+                                                          int64_t n_blocks, int bpc) {
     constexpr int KT = 8;
     __shared__ float4 S4[SYM_MAX_F4];
     __shared__ __align__(16) float rre[64][KT];
     __shared__ __align__(16) float rim[64][KT];
-    const int blk = (int)(blockIdx.x / ntile), tid = threadIdx.x;
+    // bpc blocks of at most 64 / bpc rows share the CTA: thread group `sub` (64 / bpc threads) takes one
+    const int tsub = 64 / bpc, sub = threadIdx.x / tsub, tid = threadIdx.x - sub * tsub;
+    const int64_t blk = (int64_t)(blockIdx.x / ntile) * bpc + sub;
+    const bool valid = blk < n_blocks;
     const int r0 = (int)(blockIdx.x % ntile) * KT;
-    const int n0 = block_ptr[blk], n1 = block_ptr[blk + 1];
+    const int n0 = valid ? block_ptr[blk] : 0, n1 = valid ? block_ptr[blk + 1] : 0;
     const int b = 4 * (n1 - n0);
     const int64_t base = 4 * (int64_t)n0;
     const int n4 = b * (b + 1) / 4;
@@ -316,18 +320,23 @@ __global__ void __launch_bounds__(64) k_block_apply_sym8x2(const int32_t* __rest
 #pragma unroll
     for (int q = 0; q < KT; ++q) onm |= ((r0 + q < k) && (!active || active[r0 + q])) ? 1u << q : 0u;
     if (!onm) return;  // the whole tile has retired (uniform over the CTA, before any barrier)
-    const float4* P4 = reinterpret_cast<const float4*>(pinv + poff[blk]);
-    for (int e = tid; e < n4; e += 64) S4[e] = __ldg(P4 + e);
-    for (int f = tid; f < 64 * KT; f += 64) {
+    float4* S4s = S4 + sub * (SYM_MAX_F4 / bpc);
+    float (*rre_s)[KT] = rre + sub * tsub;
+    float (*rim_s)[KT] = rim + sub * tsub;
+    if (valid) {
+        const float4* P4 = reinterpret_cast<const float4*>(pinv + poff[blk]);
+        for (int e = tid; e < n4; e += tsub) S4s[e] = __ldg(P4 + e);
+    }
+    for (int f = tid; f < tsub * KT; f += tsub) {
         const int row = f / KT, q = f - row * KT;
         float2 v = make_float2(0.f, 0.f);
         if (row < b && ((onm >> q) & 1u)) v = r[(int64_t)(r0 + q) * ld + base + row];
-        rre[row][q] = v.x;
-        rim[row][q] = v.y;
+        rre_s[row][q] = v.x;
+        rim_s[row][q] = v.y;
     }
     __syncthreads();
-    if (tid >= b) return;
-    const float2* S = reinterpret_cast<const float2*>(S4);
+    if (!valid || tid >= b) return;
+    const float2* S = reinterpret_cast<const float2*>(S4s);
     unsigned long long are[4], aim[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) are[h] = aim[h] = 0ull;
@@ -337,10 +346,10 @@ __global__ void __launch_bounds__(64) k_block_apply_sym8x2(const int32_t* __rest
     for (int j = 0; j < b; ++j) {
         const float2 a = S[j >= tid ? tj + tid : ti + j];
         const unsigned long long ax = f2pack(a.x, a.x), ay = f2pack(a.y, a.y), nay = f2pack(-a.y, -a.y);
-        const ulonglong2 re01 = *reinterpret_cast<const ulonglong2*>(&rre[j][0]);
-        const ulonglong2 re23 = *reinterpret_cast<const ulonglong2*>(&rre[j][4]);
-        const ulonglong2 im01 = *reinterpret_cast<const ulonglong2*>(&rim[j][0]);
-        const ulonglong2 im23 = *reinterpret_cast<const ulonglong2*>(&rim[j][4]);
+        const ulonglong2 re01 = *reinterpret_cast<const ulonglong2*>(&rre_s[j][0]);
+        const ulonglong2 re23 = *reinterpret_cast<const ulonglong2*>(&rre_s[j][4]);
+        const ulonglong2 im01 = *reinterpret_cast<const ulonglong2*>(&rim_s[j][0]);
+        const ulonglong2 im23 = *reinterpret_cast<const ulonglong2*>(&rim_s[j][4]);
         const unsigned long long vr[4] = {re01.x, re01.y, re23.x, re23.y};
         const unsigned long long vi[4] = {im01.x, im01.y, im23.x, im23.y};
 #pragma unroll
@@ -376,6 +385,12 @@ __global__ void __launch_bounds__(64) k_block_apply_sym8x2(const int32_t* __rest
             float2* zp = z + (int64_t)(r0 + q) * ld + base + tid;
             *zp = accumulate ? cadd(*zp, acc[q]) : acc[q];
         }
+}
+
+// blocks per 64-thread CTA of k_block_apply_sym8x2: as many as fit one thread per row
+inline int sym8_blocks_per_cta(int max_block_nodes) {
+    const int b = 4 * max_block_nodes;
+    return b <= 16 ? 4 : b <= 32 ? 2 : 1;
 }
 
 // coarse restriction: rc[r][c] = sum over the group's nodes of zv[i] * r[r][4i+3]
@@ -545,8 +560,11 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
     }
     const int32_t* bc = M.blk_c.as<int32_t>();
     if constexpr (std::is_same<T, float>::value) {
+        const int bpc = sym8_blocks_per_cta(c->max_block_nodes);
+        const unsigned grid8 = tile_grid((unsigned)((c->n_blocks + bpc - 1) / bpc), nt);
         switch (kt) {
-            case 8: k_block_apply_sym8x2<<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
+            case 8: k_block_apply_sym8x2<<<grid8, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt,
+                                                                c->n_blocks, bpc); break;
             case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
             case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
             default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
@@ -671,14 +689,18 @@ void block_inverses(cudaStream_t st, const int32_t* rp, const int32_t* col, cons
 
 template <typename T>
 void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, const C<T>* pinv, int64_t n_blocks,
-                 const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active, bool accumulate) {
+                 int max_block_nodes, const C<T>* r, C<T>* z, int k, int64_t ld, int rhs_tile, const int* active,
+                 bool accumulate) {
     const int kt = pick_ptile(k, rhs_tile);
     const int nt = (k + kt - 1) / kt;
     const unsigned grid = tile_grid((unsigned)n_blocks, nt);
     const int acc = accumulate ? 1 : 0;
     if constexpr (std::is_same<T, float>::value) {
+        const int bpc = sym8_blocks_per_cta(max_block_nodes);
+        const unsigned grid8 = tile_grid((unsigned)((n_blocks + bpc - 1) / bpc), nt);
         switch (kt) {
-            case 8: k_block_apply_sym8x2<<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
+            case 8: k_block_apply_sym8x2<<<grid8, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0,
+                                                                nullptr, acc, nt, n_blocks, bpc); break;
             case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
             case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
             default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
@@ -693,10 +715,10 @@ void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, cons
     }
     ECT_CHECK_LAUNCH();
 }
-template void block_apply<double>(cudaStream_t, const int32_t*, const int64_t*, const double2*, int64_t, const double2*,
-                                  double2*, int, int64_t, int, const int*, bool);
-template void block_apply<float>(cudaStream_t, const int32_t*, const int64_t*, const float2*, int64_t, const float2*,
-                                 float2*, int, int64_t, int, const int*, bool);
+template void block_apply<double>(cudaStream_t, const int32_t*, const int64_t*, const double2*, int64_t, int,
+                                  const double2*, double2*, int, int64_t, int, const int*, bool);
+template void block_apply<float>(cudaStream_t, const int32_t*, const int64_t*, const float2*, int64_t, int,
+                                 const float2*, float2*, int, int64_t, int, const int*, bool);
 
 // in-place dense inverse of a (n x n, complex128, row-major) on the device
 void dense_inverse(cudaStream_t st, double2* a, int64_t n) {

@@ -60,7 +60,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
                 ("mode", ctypes.c_int), ("inner_iters", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("rhs_tile", ctypes.c_int), ("timeout_s", ctypes.c_double), ("reorth", ctypes.c_int),
-                ("spmm_rows", ctypes.c_int)]
+                ("spmm_rows", ctypes.c_int), ("x0", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

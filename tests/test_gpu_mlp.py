@@ -45,7 +45,9 @@ def test_num_params(ect):
     assert ect.load_library().ect_mlp_num_params() == sum(W.size + b.size for W, b in mlp.init(0))
 
 
-@pytest.mark.parametrize("B", [128, 256])
+# 65536 rows are 512 tiles of 128: each persistent CTA takes several tiles, so the shared-memory
+# ring wraps and both TMEM accumulators are reused
+@pytest.mark.parametrize("B", [128, 256, 4096, 65536])
 def test_forward_matches_oracle(ect, B):
     p, pr, X, Xr, T = setup_case(ect, B)
     s = ect.Surrogate(batch=B)
@@ -60,9 +62,12 @@ def test_forward_matches_oracle(ect, B):
     s.close()
 
 
-def test_gradients_match_oracle(ect):
-    p, pr, X, Xr, T = setup_case(ect, 256, seed=3)
-    s = ect.Surrogate(batch=256)
+# the weight gradients contract over the batch: 256 rows is one K range per CTA, 16384 and 65536
+# split K over the CTAs (64 and 74 ranges of 4 and 14 chunks) and sum the partial products
+@pytest.mark.parametrize("B", [256, 16384, 65536])
+def test_gradients_match_oracle(ect, B):
+    p, pr, X, Xr, T = setup_case(ect, B, seed=3)
+    s = ect.Surrogate(batch=B)
     s.set_params(ect.mlp_flatten(p))
     x = torch.from_numpy(X.astype(np.float32)).cuda()
     t = torch.from_numpy(T.astype(np.float32)).cuda()

@@ -298,12 +298,12 @@ def test_coil_rhs_matches_oracle(ect, small):
             assert np.abs(B[q] - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
-def _solve_check(ect, p, ctx, M, which, opts, k=2):
+def _solve_check(ect, p, ctx, M, which, opts, k=2, x_init=None):
     n = 4 * p.mesh.n_nodes
     B = np.stack([fem.constrain_rhs(rhs.coil_rhs(p.mesh.xyz, p.mesh.tets, c.as_tuple(), p.z_pos[0]), p, which)
                   for c in p.coils][:k])
     b = dev(B)
-    x = torch.empty_like(b)
+    x = torch.empty_like(b) if x_init is None else dev(x_init)
     st = ctx.solve(WHICH[which], b, x, k, opts)
     X = x.cpu().numpy()
     t = fem.scaling(M[which])
@@ -350,6 +350,25 @@ def test_solve_batch_equals_single(ect, small):
     X2, _ = _solve_check(ect, p, ctx, M, "defect", opts, k=2)
     X1, _ = _solve_check(ect, p, ctx, M, "defect", opts, k=1)
     assert np.linalg.norm(X2[0] - X1[0]) <= 1e-6 * np.linalg.norm(X1[0])
+
+
+@pytest.mark.parametrize("mode", ["f64", "mixed"])
+def test_initial_guess(ect, small, mode):
+    """x0 = 1: the vacuum solutions as the defect system's initial guess (the warm start of a
+    deposit scan) meet the same tolerance against the oracle's matrix in fewer iterations, and a
+    guess already far inside the tolerance needs no iteration."""
+    p, ctx, M = small
+    kw = dict(restart=16, mode=ect.ECT_MODE_F64 if mode == "f64" else ect.ECT_MODE_MIXED, inner_iters=16)
+    cold = ect.default_options(tol=1e-10, **kw)
+    X0, _ = _solve_check(ect, p, ctx, M, "vacuum", cold)
+    Xd, st_cold = _solve_check(ect, p, ctx, M, "defect", cold)
+    warm = ect.default_options(tol=1e-10, x0=1, **kw)
+    Xw, st_warm = _solve_check(ect, p, ctx, M, "defect", warm, x_init=X0)
+    assert st_warm["converged"] == 2 and 0 < st_warm["iters"] <= st_cold["iters"], (st_warm, st_cold)
+    Xt, _ = _solve_check(ect, p, ctx, M, "defect", ect.default_options(tol=1e-12, **kw))
+    Xe, st_e = _solve_check(ect, p, ctx, M, "defect", warm, x_init=Xt)
+    assert st_e["iters"] == 0 and st_e["converged"] == 2, st_e
+    assert np.array_equal(Xe, Xt) or np.abs(Xe - Xt).max() <= 1e-14 * np.abs(Xt).max()
 
 
 def test_delta_z_kernel_on_oracle_solutions(ect, small):

@@ -214,7 +214,7 @@ __global__ void k_scaling(const double2* __restrict__ val, const int32_t* __rest
 __global__ void k_scale_matrix(const double2* __restrict__ val, const int32_t* __restrict__ row_ptr,
                                const int32_t* __restrict__ col, const double* __restrict__ t, int64_t n_rows,
                                int64_t nnzb, double2* __restrict__ sval, float2* __restrict__ sval32,
-                               float2* __restrict__ sval32lo, float2* __restrict__ sval32t) {
+                               float2* __restrict__ sval32lo, float* __restrict__ sval32p) {
     int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (slot >= nnzb) return;
     int row = row_of_slot(row_ptr, n_rows, (int)slot);
@@ -236,7 +236,9 @@ __global__ void k_scale_matrix(const double2* __restrict__ val, const int32_t* _
             if (sval32) {
                 const float2 h = make_float2((float)v.x, (float)v.y);
                 sval32[16 * slot + 4 * p + r] = h;
-                sval32t[16 * slot + 4 * r + p] = h;
+                float* q = sval32p + 32 * slot + 16 * (p >> 1) + 4 * r + (p & 1);  // row-pair layout
+                q[0] = h.x;
+                q[2] = h.y;
                 sval32lo[16 * slot + 4 * p + r] =
                     make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
             }
@@ -264,8 +266,9 @@ void scale_matrix(ect_ctx* c, Matrix& M, bool f32) {
                                                         c->col.as<int32_t>(), M.t.as<double>(), N, nnzb,
                                                         M.sval.as<double2>(), f32 ? M.sval32.as<float2>() : nullptr,
                                                         f32 ? M.sval32lo.as<float2>() : nullptr,
-                                                        f32 ? M.sval32t.as<float2>() : nullptr);
+                                                        f32 ? M.sval32p.as<float>() : nullptr);
     ECT_CHECK_LAUNCH();
+    ++M.val_gen;
 }
 
 void alloc_values(ect_ctx* c, Matrix& M, bool f32) {
@@ -276,12 +279,14 @@ void alloc_values(ect_ctx* c, Matrix& M, bool f32) {
     if (f32) {
         M.sval32.alloc(sizeof(float2) * 16 * nnzb);
         M.sval32lo.alloc(sizeof(float2) * 16 * nnzb);
-        M.sval32t.alloc(sizeof(float2) * 16 * nnzb);
+        M.sval32p.alloc(sizeof(float2) * 16 * nnzb);
     } else {
         M.sval32.release();
         M.sval32lo.release();
-        M.sval32t.release();
+        M.sval32p.release();
     }
+    M.sval32t.release();  // rebuilt from sval32 on demand
+    M.t_gen = 0;
 }
 
 }  // namespace

@@ -205,10 +205,16 @@ void staged_plan_build(cudaStream_t st, StagedPlan& P, const std::vector<int32_t
                        const std::vector<int32_t>& col, int64_t n_rows, int64_t n_cols, int rows);
 // y[r] = A x[r] (b == nullptr) or y[r] = b[r] - A x[r] for k right-hand sides
 // (b may equal y: in-place t -= A x).  x has leading dimension ldx (column
-// space), b and y ldy (row space).  FP32 complex values, 16 per block.
-void bsr_spmm_staged_f32(cudaStream_t st, const StagedPlan& P, const int32_t* rp, const float2* val,
+// space), b and y ldy (row space).  FP32 complex values in the row-pair
+// layout (to_pair_layout), 8 float4 per block.
+void bsr_spmm_staged_f32(cudaStream_t st, const StagedPlan& P, const int32_t* rp, const float4* val,
                          const float2* x, int64_t ldx, const float2* b, float2* y, int64_t ldy, int k,
                          const int* active);
+// Block layouts of FP32 4x4 complex blocks stored row-major (16 float2 per block):
+// the row-pair layout of the staged SpMM and the transposed layout of the
+// warp-per-row SpMM.
+void to_pair_layout(cudaStream_t st, const float2* in, float4* out, int64_t nnzb);
+void to_transposed_layout(cudaStream_t st, const float2* in, float2* out, int64_t nnzb);
 // Read and clear the flag that a staged kernel sets when its bounded wait on
 // a bulk copy expired (1 = expired).  Synchronises the stream.
 int staged_take_error(cudaStream_t st);
@@ -219,6 +225,22 @@ void bsr_spmm_colwarp_f32(cudaStream_t st, const int32_t* rp, const int32_t* col
                           const float2* x, int64_t ldx, const float2* b, float2* y, int64_t ldy, int k,
                           const int* active);
 constexpr int SPMM_COLWARP = -2;  // ect_options.spmm_rows value selecting it
+
+// Paired single-precision FMA (two lanes of a 64-bit register pair per
+// instruction, sm_100 family): d = a * b + c elementwise.
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 // default target rows per tile of the staged SpMM
 constexpr int STAGED_ROWS_DEFAULT = 32;
 
@@ -240,7 +262,13 @@ struct Matrix {
     DevBuf sval;           // double2[nnzb*16] scaled  S = T M T
     DevBuf sval32;         // float2 [nnzb*16] scaled
     DevBuf sval32lo;       // float2 [nnzb*16] FP32 remainder: sval ~= sval32 + sval32lo to ~2^-48
-    DevBuf sval32t;        // float2 [nnzb*16] FP32 scaled, each block transposed (column-major)
+    DevBuf sval32p;        // float4 [nnzb*8] FP32 scaled, row-pair layout (the staged SpMM's input):
+                           //   per block, rows (2P, 2P+1) and column c at float4 4P + c:
+                           //   (re S[2P][c], re S[2P+1][c], im S[2P][c], im S[2P+1][c])
+    DevBuf sval32t;        // float2 [nnzb*16] FP32 scaled, each block transposed (column-major);
+                           //   built from sval32 when the warp-per-row SpMM is selected
+    uint64_t val_gen = 0;  // bumped whenever the scaled values are rewritten
+    uint64_t t_gen = 0;    // val_gen that sval32t was built from (0: never)
     DevBuf t;              // double[4N] scaling
     DevBuf pinv;           // double2 block inverses (column-major per block)
     DevBuf pinv32;         // float2  block inverses
@@ -284,7 +312,7 @@ struct Matrix {
         h_void.clear();
         n_faces = 0;
         for (DevBuf* b : {&tvoid, &s_ptr, &s_ent, &s_geo}) b->release();
-        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &sval32lo, &sval32t, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
+        for (DevBuf* b : {&sigma, &nu, &fixmask, &val, &sval, &sval32, &sval32lo, &sval32p, &sval32t, &t, &pinv, &pinv32, &einv, &einv32, &blk_c,
                           &agg_lo, &agg_hi, &zv, &zv32, &rc, &zc, &gpart})
             b->release();
     }

@@ -10,9 +10,10 @@
 //   * warp 1 (one thread) issues the tcgen05.mma instructions of each stage
 //     into one of two TMEM accumulators of N fp32 columns, and frees the stage
 //     with tcgen05.commit when its MMAs complete;
-//   * warps 2-5 read the finished accumulator (TMEM lane quarter warp % 4,
-//     thread <-> tile row) and run the epilogue while the MMAs of the next tile
-//     fill the other accumulator.
+//   * warps 2-9 read the finished accumulator (TMEM lane quarter warp % 4,
+//     thread <-> tile row; the two warps of a quarter take one half of the
+//     columns each) and run the epilogue while the MMAs of the next tile fill
+//     the other accumulator.
 // A work item is a 128-row tile and a range of K chunks: the weight-gradient
 // GEMM (M = 256, K = batch) splits K over the CTAs and writes fp32 partial
 // products that a second kernel sums in a fixed order.  Every mbarrier wait
@@ -33,10 +34,11 @@ enum Mode : int {
     FWD_INFER = 4,   // x = silu(acc + bias) -> Xc only (inference: nothing kept for a backward pass)
 };
 
-constexpr int PIPE_THREADS = 192;      // warp 0 copies, warp 1 issues MMAs, warps 2-5 run the epilogue
+constexpr int EPI_WARPS = 8;           // two per TMEM lane quarter
+constexpr int PIPE_THREADS = 64 + 32 * EPI_WARPS;  // warp 0 copies, warp 1 issues MMAs, the rest run the epilogue
 constexpr int PIPE_MAX_STAGES = 8;
 constexpr int KCH_MAX = 64;            // K elements per stage
-constexpr int EPI_BYTES = 4 * 1024;    // per epilogue warp: 16 columns x 32 rows of bf16
+constexpr int EPI_BYTES = EPI_WARPS * 1024;  // per epilogue warp: 16 columns x 32 rows of bf16
 constexpr int PIPE_SMEM_MAX = 232448 - 2048;  // dynamic shared memory (the static barriers aside)
 constexpr uint32_t RESIDENT_B_MAX = 128 * 1024;
 
@@ -64,9 +66,10 @@ struct GemmArgs {
     uint32_t stage_bytes;
 };
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// fast reciprocal division: the results are rounded to bf16 (8-bit mantissa) or feed a bf16 GEMM
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad_f(float z) {
-    const float s = 1.0f / (1.0f + __expf(-z));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
 }
 
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_gemm_tc(GemmArgs g) {
         tc05::mbar_init(&bfull, 1);
         for (int a = 0; a < 2; ++a) {
             tc05::mbar_init(&tfull[a], 1);
-            tc05::mbar_init(&tempty[a], 4);  // one arrival per epilogue warp
+            tc05::mbar_init(&tempty[a], EPI_WARPS);  // one arrival per epilogue warp
         }
         tc05::mbar_init(&drain, 1);
         tc05::fence_barrier_init();
@@ -210,8 +213,10 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_gemm_tc(GemmArgs g) {
             tc05::mma_commit(&drain);  // all MMAs issued here complete before the TMEM is freed
             drain_wait(&drain, 0);
         }
-    } else {  // ---- epilogue: warps 2..5, TMEM lane quarter warp % 4
-        const int q = warp & 3;
+    } else {  // ---- epilogue: warps 2..9, TMEM lane quarter warp % 4, column half (warp - 2) / 4
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int ngrp = N / 16, gper = (ngrp + 1) / 2;  // 16-column groups, per half
+        const int cbeg = 16 * min(ngrp, half * gper), cend = 16 * min(ngrp, (half + 1) * gper);
         uint8_t* tb = epi + (warp - 2) * 1024;
         int lt = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x, ++lt) {
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_gemm_tc(GemmArgs g) {
             tc05::fence_after_sync();
             const int rowbase = 128 * mt + 32 * q, row = rowbase + lane;
             const uint32_t taddr = tmem + (uint32_t)acc * ncol + ((uint32_t)(32 * q) << 16);
-            for (int c0 = 0; c0 < N; c0 += 16) {
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 float v[16];
                 tc05::tmem_ld16(taddr + (uint32_t)c0, v);
                 if (g.mode == BWD_DW) {

@@ -222,7 +222,8 @@ struct MgLevel {
     const int32_t* col = nullptr;
     const double2* val64 = nullptr;
     const float2* val32 = nullptr;
-    DevBuf rp_own, col_own, val_own, val32_own;
+    const float4* val32p = nullptr;          // FP32 values in the staged SpMM's row-pair layout
+    DevBuf rp_own, col_own, val_own, val32_own, val32p_own;
     std::vector<int32_t> h_rp, h_col, h_agg_ptr;
     std::vector<uint8_t> h_free;             // 4n: unknown carries a near-null weight
     const int32_t* d_agg_ptr = nullptr;
@@ -232,7 +233,7 @@ struct MgLevel {
     const float2* d_pinv32 = nullptr;
     DevBuf agg_ptr_own, pinv_off_own, pinv32_off_own, pinv64_own, pinv32_own;
     DevBuf node_agg, clo, chi, w64, w32;
-    DevBuf ap_ptr, ap_col, ap_val64, ap_val32;  // AP = A P (this level's rows, next level's columns)
+    DevBuf ap_ptr, ap_col, ap_val64, ap_val32, ap_val32p;  // AP = A P (this level's rows, next level's columns)
     std::vector<int32_t> h_ap_ptr, h_ap_col;
     bool has_ap = false;
     StagedPlan plan, ap_plan;                // staged FP32 SpMM tilings of A (levels > 0) and AP
@@ -359,6 +360,8 @@ void build_ap(cudaStream_t st, MgLevel& L, const std::vector<int32_t>& nagg, boo
     if (f32) {
         L.ap_val32.alloc(sizeof(float2) * 16 * std::max<int64_t>(nnz, 1));
         to_f32(st, L.ap_val64.as<double2>(), L.ap_val32.as<float2>(), 16 * nnz);
+        L.ap_val32p.alloc(sizeof(float2) * 16 * std::max<int64_t>(nnz, 1));
+        to_pair_layout(st, L.ap_val32.as<float2>(), L.ap_val32p.as<float4>(), nnz);
     }
     ECT_CUDA(cudaStreamSynchronize(st));  // the host arrays above go out of scope
     L.has_ap = true;
@@ -410,6 +413,7 @@ void mg_setup(ect_ctx* c, int which, bool f32) {
         L.col = c->col.as<int32_t>();
         L.val64 = M.sval.as<double2>();
         L.val32 = f32 ? M.sval32.as<float2>() : nullptr;
+        L.val32p = f32 ? M.sval32p.as<float4>() : nullptr;
         L.h_rp = c->h_row_ptr;
         L.h_col = c->h_col;
         L.h_agg_ptr = c->h_block_ptr;
@@ -576,6 +580,9 @@ void mg_setup(ect_ctx* c, int which, bool f32) {
             Lc.val32_own.alloc(sizeof(float2) * 16 * nnzc);
             to_f32(st, Lc.val64, Lc.val32_own.as<float2>(), 16 * nnzc);
             Lc.val32 = Lc.val32_own.as<float2>();
+            Lc.val32p_own.alloc(sizeof(float2) * 16 * std::max<int64_t>(nnzc, 1));
+            to_pair_layout(st, Lc.val32, Lc.val32p_own.as<float4>(), nnzc);
+            Lc.val32p = Lc.val32p_own.as<float4>();
         }
         Lc.h_free.resize(4 * na);
         std::vector<double> w(4 * na);
@@ -642,8 +649,8 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
             bsr_spmm_colwarp_f32(st, L.rp, L.col, G->val32t, L.n, (const float2*)z, ld, (const float2*)r, (float2*)t,
                                  ld, k, active);
         else if (staged && L.n > WARP_ROW_MAX_NODES)
-            bsr_spmm_staged_f32(st, *plan, L.rp, (const float2*)val, (const float2*)z, ld, (const float2*)r,
-                                (float2*)t, ld, k, active);
+            bsr_spmm_staged_f32(st, *plan, L.rp, L.val32p, (const float2*)z, ld, (const float2*)r, (float2*)t, ld, k,
+                                active);
         else if (L.n <= WARP_ROW_MAX_NODES)
             bsr_spmv_warp<T>(st, L.rp, L.col, val, L.n, z, r, t, k, ld, tile, active);
         else if (std::is_same<T, double>::value)
@@ -664,7 +671,7 @@ void cycle(cudaStream_t st, Multigrid* G, size_t l, const C<T>* r, C<T>* z, int 
                                                                         active);
         if (L.has_ap) {
             if (std::is_same<T, float>::value && G->staged_rows > 0 && L.ap_plan.ok)
-                bsr_spmm_staged_f32(st, L.ap_plan, L.ap_ptr.as<int32_t>(), L.ap_val32.as<float2>(),
+                bsr_spmm_staged_f32(st, L.ap_plan, L.ap_ptr.as<int32_t>(), L.ap_val32p.as<float4>(),
                                     (const float2*)zn, ldn, (const float2*)t, (float2*)t, ld, k, active);
             else
                 ap_update<T>(st, L, zn, ldn, t, ld, k, tile, active);
@@ -697,9 +704,14 @@ void staged_prepare(ect_ctx* c, int which) {
     Matrix& M = ctx_mat(c, which);
     Multigrid* G = M.mg;
     if (rows <= 0) {
+        if (rows == SPMM_COLWARP && M.has_f32 && M.t_gen != M.val_gen) {  // transposed blocks, on demand
+            if (!M.sval32t.p) M.sval32t.alloc(sizeof(float2) * 16 * c->nnzb);
+            to_transposed_layout(c->stream, M.sval32.as<float2>(), M.sval32t.as<float2>(), c->nnzb);
+            M.t_gen = M.val_gen;
+        }
         if (G) {
             G->staged_rows = rows == SPMM_COLWARP ? SPMM_COLWARP : -1;
-            G->val32t = M.sval32t.as<float2>();
+            G->val32t = rows == SPMM_COLWARP ? M.sval32t.as<float2>() : nullptr;
         }
         return;
     }

@@ -270,22 +270,6 @@ __global__ void __launch_bounds__(64) k_block_apply_sym(const int32_t* __restric
         }
 }
 
-// Paired single-precision FMA (two lanes of a 64-bit register pair per
-// instruction, sm_100 family): d = a * b + c elementwise.
-__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
 // k_block_apply_sym for a full tile of 8 right-hand sides with paired FMAs.
 // The tile is kept planar in shared memory (real parts of the 8 right-hand
 // sides of a row, then their imaginary parts), so two right-hand sides are

@@ -105,7 +105,7 @@ struct PipeArgs {
     const int32_t* meta_off;
     const uint8_t* meta;
     const int32_t* cols;
-    const float2* val;
+    const float4* val;  // row-pair layout, 8 float4 per block
     const float2* x;
     int64_t ldx;
     const float2* b;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(STG_THREADS, 1) k_spmm_pipe(const PipeArgs a) 
                 const int mo0 = a.meta_off[tile], mo1 = a.meta_off[tile + 1];
                 const uint32_t mbytes = (uint32_t)(blk1 - blk0) * 128u, tbytes = (uint32_t)(mo1 - mo0) * 16u;
                 tc05::mbar_expect_tx(&full[s], mbytes + tbytes);
-                tc05::bulk_g2s(st, a.val + 16 * (int64_t)blk0, mbytes, &full[s]);
+                tc05::bulk_g2s(st, a.val + 8 * (int64_t)blk0, mbytes, &full[s]);
                 tc05::bulk_g2s(st + a.off_meta, a.meta + 16 * (int64_t)mo0, tbytes, &full[s]);
             }
             unsigned char* xs = st + a.off_x;
@@ -195,9 +195,12 @@ __global__ void __launch_bounds__(STG_THREADS, 1) k_spmm_pipe(const PipeArgs a) 
     }
     // ---- consumers: a warp takes 2 block rows at a time, 16 lanes per row, the two
     // half-warps on alternate blocks of the row; lane (pp, qq) of a row computes
-    // scalar rows 2pp, 2pp + 1 for right-hand sides 2qq, 2qq + 1 (four complex
-    // accumulators), so each 16-byte shared-memory load feeds two outputs' worth
-    // of multiply-adds; the half-warps' partial sums meet in one shuffle
+    // the scalar row pair (2pp, 2pp + 1) for right-hand sides 2qq, 2qq + 1.  The
+    // blocks are staged in the row-pair layout, so one 16-byte load holds column
+    // c of both rows, (re, re, im, im): paired FMAs (fma.rn.f32x2) take the two
+    // rows at once against the broadcast x entry, with the products of the
+    // imaginary parts summed apart and subtracted at the end.  The half-warps'
+    // partial sums meet in one shuffle.
     const int cw = warp - PRODUCER_WARPS, hh = lane >> 4, g = (lane >> 3) & 1, pp = (lane >> 2) & 1, qq = lane & 3;
     const int p0 = 2 * pp, q0 = 2 * qq;
     int64_t j = 0;
@@ -228,39 +231,56 @@ __global__ void __launch_bounds__(STG_THREADS, 1) k_spmm_pipe(const PipeArgs a) 
             float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;  // in flight during the row
             if (a.b && row_ok && st0) b0 = *reinterpret_cast<const float4*>(a.b + e0);
             if (a.b && row_ok && st1) b1 = *reinterpret_cast<const float4*>(a.b + e1);
-            float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;  // (row p0+., rhs q0+.)
+            // per right-hand side u (q0) and v (q0 + 1), each over the row pair:
+            // sum re(m) re(x), sum im(m) im(x), sum of the imaginary part
+            unsigned long long rpu = 0ull, rnu = 0ull, imu = 0ull, rpv = 0ull, rnv = 0ull, imv = 0ull;
             for (int sb = s0 + hh; sb < s1; sb += 2) {  // the two half-warps take alternate blocks
                 const uint32_t lc = lcs[sb];
-                const float4* m = reinterpret_cast<const float4*>(mb + (uint32_t)sb * 128u);
-                const float4 m0a = m[0], m0b = m[1], m1a = m[2], m1b = m[3];  // rows p0, p0 + 1
+                const ulonglong2* m = reinterpret_cast<const ulonglong2*>(mb + (uint32_t)sb * 128u);
                 const float4* u = reinterpret_cast<const float4*>(x0 + lc * 32u);
                 const float4* v = reinterpret_cast<const float4*>(x1 + lc * 32u);
                 const float4 ua = u[0], ub = u[1], va = v[0], vb = v[1];
-                cfma4(c00, m0a, m0b, ua, ub);
-                cfma4(c01, m0a, m0b, va, vb);
-                cfma4(c10, m1a, m1b, ua, ub);
-                cfma4(c11, m1a, m1b, va, vb);
+                const float xu[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+                const float xv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const ulonglong2 mc = m[cc];  // (re row p0, re row p0 + 1), (im, im) of column cc
+                    const unsigned long long ur = f2pack(xu[2 * cc], xu[2 * cc]), ui = f2pack(xu[2 * cc + 1], xu[2 * cc + 1]);
+                    const unsigned long long vr = f2pack(xv[2 * cc], xv[2 * cc]), vi = f2pack(xv[2 * cc + 1], xv[2 * cc + 1]);
+                    rpu = ffma2(mc.x, ur, rpu);
+                    rnu = ffma2(mc.y, ui, rnu);
+                    imu = ffma2(mc.x, ui, imu);
+                    imu = ffma2(mc.y, ur, imu);
+                    rpv = ffma2(mc.x, vr, rpv);
+                    rnv = ffma2(mc.y, vi, rnv);
+                    imv = ffma2(mc.x, vi, imv);
+                    imv = ffma2(mc.y, vr, imv);
+                }
+            }
+            float o[8];  // (re, im) of rows p0, p0 + 1 for u, then for v
+            {
+                float a0, a1, n0, n1, i0, i1;
+                f2unpack(rpu, a0, a1);
+                f2unpack(rnu, n0, n1);
+                f2unpack(imu, i0, i1);
+                o[0] = a0 - n0, o[1] = i0, o[2] = a1 - n1, o[3] = i1;
+                f2unpack(rpv, a0, a1);
+                f2unpack(rnv, n0, n1);
+                f2unpack(imv, i0, i1);
+                o[4] = a0 - n0, o[5] = i0, o[6] = a1 - n1, o[7] = i1;
             }
 #pragma unroll
-            for (int o = 0; o < 2; ++o) {  // add the other half-warp's partial sums (lane ^ 16)
-                float2* cc = o == 0 ? &c00 : &c01;
-                cc->x += __shfl_xor_sync(0xffffffffu, cc->x, 16);
-                cc->y += __shfl_xor_sync(0xffffffffu, cc->y, 16);
-            }
-            c10.x += __shfl_xor_sync(0xffffffffu, c10.x, 16);
-            c10.y += __shfl_xor_sync(0xffffffffu, c10.y, 16);
-            c11.x += __shfl_xor_sync(0xffffffffu, c11.x, 16);
-            c11.y += __shfl_xor_sync(0xffffffffu, c11.y, 16);
+            for (int e = 0; e < 8; ++e) o[e] += __shfl_xor_sync(0xffffffffu, o[e], 16);  // the other half-warp
             if (!row_ok || hh) continue;
             if (st0) {
-                float4 o = make_float4(c00.x, c00.y, c10.x, c10.y);
-                if (a.b) o = make_float4(b0.x - o.x, b0.y - o.y, b0.z - o.z, b0.w - o.w);
-                *reinterpret_cast<float4*>(a.y + e0) = o;
+                float4 r = make_float4(o[0], o[1], o[2], o[3]);
+                if (a.b) r = make_float4(b0.x - r.x, b0.y - r.y, b0.z - r.z, b0.w - r.w);
+                *reinterpret_cast<float4*>(a.y + e0) = r;
             }
             if (st1) {
-                float4 o = make_float4(c01.x, c01.y, c11.x, c11.y);
-                if (a.b) o = make_float4(b1.x - o.x, b1.y - o.y, b1.z - o.z, b1.w - o.w);
-                *reinterpret_cast<float4*>(a.y + e1) = o;
+                float4 r = make_float4(o[4], o[5], o[6], o[7]);
+                if (a.b) r = make_float4(b1.x - r.x, b1.y - r.y, b1.z - r.z, b1.w - r.w);
+                *reinterpret_cast<float4*>(a.y + e1) = r;
             }
         }
         __syncwarp();
@@ -370,7 +390,37 @@ void staged_plan_build(cudaStream_t st, StagedPlan& P, const std::vector<int32_t
     P.ok = true;
 }
 
-void bsr_spmm_staged_f32(cudaStream_t st, const StagedPlan& P, const int32_t* rp, const float2* val,
+// row-pair layout: block b, float4 4P + c = (re A[2P][c], re A[2P+1][c], im A[2P][c], im A[2P+1][c])
+__global__ void k_to_pair(const float2* __restrict__ in, float4* __restrict__ out, int64_t nnzb) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (block, P, c)
+    if (e >= 8 * nnzb) return;
+    const int64_t b = e >> 3;
+    const int P = (int)(e >> 2) & 1, c = (int)e & 3;
+    const float2 lo = in[16 * b + 4 * (2 * P) + c], hi = in[16 * b + 4 * (2 * P + 1) + c];
+    out[e] = make_float4(lo.x, hi.x, lo.y, hi.y);
+}
+
+__global__ void k_to_transposed(const float2* __restrict__ in, float2* __restrict__ out, int64_t nnzb) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (block, row p, column r)
+    if (e >= 16 * nnzb) return;
+    const int64_t b = e >> 4;
+    const int p = (int)(e >> 2) & 3, r = (int)e & 3;
+    out[16 * b + 4 * r + p] = in[e];
+}
+
+void to_pair_layout(cudaStream_t st, const float2* in, float4* out, int64_t nnzb) {
+    if (nnzb <= 0) return;
+    k_to_pair<<<grid_for(8 * nnzb, 256), 256, 0, st>>>(in, out, nnzb);
+    ECT_CHECK_LAUNCH();
+}
+
+void to_transposed_layout(cudaStream_t st, const float2* in, float2* out, int64_t nnzb) {
+    if (nnzb <= 0) return;
+    k_to_transposed<<<grid_for(16 * nnzb, 256), 256, 0, st>>>(in, out, nnzb);
+    ECT_CHECK_LAUNCH();
+}
+
+void bsr_spmm_staged_f32(cudaStream_t st, const StagedPlan& P, const int32_t* rp, const float4* val,
                          const float2* x, int64_t ldx, const float2* b, float2* y, int64_t ldy, int k,
                          const int* active) {
     ECT_REQUIRE(P.ok, ECT_ERR_STATE, "staged SpMM plan not built (internal)");

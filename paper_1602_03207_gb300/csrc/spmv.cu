@@ -441,12 +441,13 @@ void spmv_f32(ect_ctx* c, int which, const float2* x, float2* y, int k, int64_t 
     Matrix& M = ctx_mat(c, which);
     ECT_REQUIRE(M.assembled && M.has_f32, ECT_ERR_STATE, "FP32 matrix not assembled (use ECT_F32 in ect_assemble)");
     if (c->staged_rows == SPMM_COLWARP && rhs_tile != -1) {
+        ECT_REQUIRE(M.t_gen == M.val_gen, ECT_ERR_STATE, "transposed FP32 blocks not prepared (internal)");
         bsr_spmm_colwarp_f32(c->stream, c->row_ptr.as<int32_t>(), c->col.as<int32_t>(), M.sval32t.as<float2>(),
                              c->n_nodes, x, ldx, nullptr, y, ldx, k, active);
         return;
     }
     if (c->staged_rows > 0 && rhs_tile != -1 && c->fine_plan.ok && c->fine_plan.rows == c->staged_rows) {
-        bsr_spmm_staged_f32(c->stream, c->fine_plan, c->row_ptr.as<int32_t>(), M.sval32.as<float2>(), x, ldx,
+        bsr_spmm_staged_f32(c->stream, c->fine_plan, c->row_ptr.as<int32_t>(), M.sval32p.as<float4>(), x, ldx,
                             nullptr, y, ldx, k, active);
         return;
     }

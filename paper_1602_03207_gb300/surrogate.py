@@ -56,9 +56,11 @@ def load_samples(path):
 class DatasetGenerator:
     """Solver-generated (deposit parameters -> Delta Z_11 along the probe path) samples."""
 
-    def __init__(self, mesh, background, coil, z_pos, make_defect, options=None):
+    def __init__(self, mesh, background, coil, z_pos, make_defect, options=None, tune=False):
         """mesh/background: an input problem without deposit (its mesh, sigma, nu, physics);
-        make_defect(seed) -> (params(6,), sigma_d(T,), nu_d(T,)) on the same mesh."""
+        make_defect(seed) -> (params(6,), sigma_d(T,), nu_d(T,)) on the same mesh.
+        tune: pick the solver options (tiles, SpMM variant, Krylov lengths, Gram-Schmidt
+        variant, subdomain split) with ect_autotune on the background system first."""
         import torch
         self.torch = torch
         self.p = background
@@ -79,6 +81,8 @@ class DatasetGenerator:
         self.ctx.coil_rhs(coil, self.z, self.B)
         self.U0 = torch.empty_like(self.B)
         self.Ud = torch.empty_like(self.B)
+        if tune:
+            self.opts, _ = self.ctx.autotune(E.ECT_VACUUM, self.B, self.U0, k, self.opts)
         self.stats0 = self.ctx.solve(E.ECT_VACUUM, self.B, self.U0, k, self.opts)
         self.current = coil.current
         # the deposit changes the fields near it only: each defect solve starts from the
@@ -220,7 +224,7 @@ def run(out_path, budget_s=600.0, shape=(50, 50, 100), n_pos=128, held_out=0.1, 
     background, z, make_defect = deposit_workload(shape, n_pos=n_pos)
     opts = E.default_options(tol=tol, mode=E.ECT_MODE_MIXED, restart=16, inner_iters=12, max_iters=300)
     t0 = time.perf_counter()
-    gen = DatasetGenerator(None, background, background.coils[0], z, make_defect, opts)
+    gen = DatasetGenerator(None, background, background.coils[0], z, make_defect, opts, tune=True)
     setup_s = time.perf_counter() - t0
     samples = gen.run(range(max_seed), out_path, budget_s=budget_s)
     seeds = sorted(samples)
@@ -244,6 +248,9 @@ def run(out_path, budget_s=600.0, shape=(50, 50, 100), n_pos=128, held_out=0.1, 
     solve_s = float(np.median([samples[s]["seconds"] for s in seeds]))
     return {"samples": len(seeds), "train": len(train), "held_out": len(test), "positions": n_pos,
             "mesh_nodes": int(np.prod(shape)), "solver_tol": tol, "setup_s": setup_s,
+            "solver_options": {f: getattr(gen.opts, f) for f in ("restart", "inner_iters", "reorth", "rhs_tile",
+                                                                 "spmm_rows")},
+            "block_split": gen.ctx.block_split(),
             "solver_s_per_deposit": solve_s, "surrogate_s_per_deposit": infer_s,
             "speedup": solve_s / max(infer_s, 1e-12), "train_steps": fit["steps"], "train_s": fit["seconds"],
             "loss_history": fit["history"][-5:],

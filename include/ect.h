@@ -297,8 +297,7 @@ int ect_delta_z(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_
  * 64 positions (n_pos > 64 returns ECT_ERR_ARG); every GPU that loads the
  * library keeps it until the process exits.  The first call on a device looks
  * up the array's device address (with that device current) and keeps it for
- * the life of the process; make that first call before any stream capture.
- * cudaDeviceReset invalidates the kept address: do not call this function
+ * the life of the process.  cudaDeviceReset invalidates the kept address: do not call this function
  * on a device after resetting it.  All calls share the array: calls that
  * overlap on the GPU race.  Synchronises the context stream. */
 int ect_delta_z_static(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_b, const double* h_current,

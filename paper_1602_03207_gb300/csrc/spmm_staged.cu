@@ -19,13 +19,14 @@
 //     q][column][4 complex] in the stage; list entries are mostly consecutive
 //     nodes, so a warp's copies are contiguous runs); all of it completes on
 //     the stage's "full" mbarrier;
-//   * consumer warps: two block rows per warp, four lane groups per row on
-//     every fourth block; lane qq of a group owns the four scalar rows of
-//     right-hand sides 2qq, 2qq + 1, reads each of its blocks whole (row-pair
-//     layout) and the x values of its two right-hand sides at the block's
-//     column node from shared memory, multiplies with paired FMAs, and after
-//     the groups' sums meet stores y (or b - A x) directly; then the warp
-//     arrives on the stage's "empty" mbarrier.
+//   * consumer warps: two block rows per warp, the half-warps on alternate
+//     blocks of a row; lane (pp, qq) of an eight-lane group owns scalar rows
+//     2pp, 2pp + 1 of right-hand sides 2qq, 2qq + 1,
+//     reads those two rows of each block and the x values of its two right-
+//     hand sides at the block's column node from shared memory (one 16-byte
+//     load feeds two outputs), keeps four complex accumulators and stores y
+//     (or b - A x) directly, then the warp arrives on the stage's "empty"
+//     mbarrier.
 // There is no CTA-wide barrier in the loop: the matrix streams from HBM while
 // earlier stages are computed, every x value of a tile's list is read once
 // per item, and no gather goes through L1.  All waits are bounded: on expiry
@@ -192,21 +193,16 @@ __global__ void __launch_bounds__(STG_THREADS, 1) k_spmm_pipe(const PipeArgs a) 
         cp_async_wait<0>();
         return;
     }
-    // ---- consumers: a warp takes 2 block rows at a time, 16 lanes per row in
-    // four groups of four that take every fourth block of the row; lane qq of a
-    // group computes all four scalar rows for right-hand sides 2qq, 2qq + 1.
-    // The blocks are staged in the row-pair layout, so one 16-byte load holds
-    // column c of rows 2P and 2P + 1, (re, re, im, im): paired FMAs
-    // (fma.rn.f32x2) take both rows at once against the broadcast x entry, with
-    // the products of the imaginary parts summed apart and subtracted at the
-    // end.  Per block a lane loads the whole block (128 bytes) and the x
-    // entries of its two right-hand sides (64 bytes), so the four lanes of a
-    // block move 768 bytes of shared memory for 32 complex multiply-adds each.
-    // The four groups' partial sums meet in two shuffles; the lanes of a row
-    // then store one 16-byte piece each.
-    const int cw = warp - PRODUCER_WARPS, g = lane >> 4, grp = (lane >> 2) & 3, qq = lane & 3;
-    const int q0 = 2 * qq;
-    const int qo = q0 + (grp >> 1), po = 2 * (grp & 1);  // the output piece of this lane: rhs qo, rows po, po + 1
+    // ---- consumers: a warp takes 2 block rows at a time, 16 lanes per row, the two
+    // half-warps on alternate blocks of the row; lane (pp, qq) of a row computes
+    // the scalar row pair (2pp, 2pp + 1) for right-hand sides 2qq, 2qq + 1.  The
+    // blocks are staged in the row-pair layout, so one 16-byte load holds column
+    // c of both rows, (re, re, im, im): paired FMAs (fma.rn.f32x2) take the two
+    // rows at once against the broadcast x entry, with the products of the
+    // imaginary parts summed apart and subtracted at the end.  The half-warps'
+    // partial sums meet in one shuffle.
+    const int cw = warp - PRODUCER_WARPS, hh = lane >> 4, g = (lane >> 3) & 1, pp = (lane >> 2) & 1, qq = lane & 3;
+    const int p0 = 2 * pp, q0 = 2 * qq;
     int64_t j = 0;
     for (int64_t item = blockIdx.x; item < a.n_items; item += G, ++j) {
         const int s = (int)(j % S);
@@ -217,29 +213,30 @@ __global__ void __launch_bounds__(STG_THREADS, 1) k_spmm_pipe(const PipeArgs a) 
         const unsigned char* st = base + (size_t)s * a.stage_bytes;
         const int r0 = (int)(item % a.nrt) * STG_KT;
         const int kt = min(STG_KT, a.k - r0);
-        const bool sto = qo < kt && (!a.active || a.active[r0 + qo]);
-        const bool any = (q0 < kt && (!a.active || a.active[r0 + q0])) ||
-                         (q0 + 1 < kt && (!a.active || a.active[r0 + q0 + 1]));
+        const bool st0 = q0 < kt && (!a.active || a.active[r0 + q0]);
+        const bool st1 = q0 + 1 < kt && (!a.active || a.active[r0 + q0 + 1]);
         const int32_t* hdr = reinterpret_cast<const int32_t*>(st + a.off_meta);
         const int row0 = hdr[0], row1 = hdr[1];  // from the staged metadata record
         const int32_t* rps = hdr + 4;
         const uint16_t* lcs = reinterpret_cast<const uint16_t*>(rps + (row1 - row0 + 1));
+        const unsigned char* mb = st + (uint32_t)pp * 64u;
         const unsigned char* x0 = st + a.off_x + (uint32_t)q0 * a.xq;
         const unsigned char* x1 = x0 + a.xq;
         for (int i2 = row0 + 2 * cw; i2 < row1; i2 += 2 * CONSUMER_WARPS) {
             const int i = i2 + g;
             const bool row_ok = i < row1;
-            const int s0 = row_ok && any ? rps[i - row0] : 0, s1 = row_ok && any ? rps[i - row0 + 1] : 0;
-            const int64_t eo = (int64_t)(r0 + qo) * a.ldy + 4 * (int64_t)i + po;
-            float4 bo = make_float4(0.f, 0.f, 0.f, 0.f);  // in flight during the row
-            if (a.b && row_ok && sto) bo = *reinterpret_cast<const float4*>(a.b + eo);
-            // [row pair P]: per right-hand side u (q0) and v (q0 + 1), sum re(m) re(x),
-            // sum im(m) im(x) and the imaginary part, each over the two rows of P
-            unsigned long long rpu[2] = {0ull, 0ull}, rnu[2] = {0ull, 0ull}, imu[2] = {0ull, 0ull};
-            unsigned long long rpv[2] = {0ull, 0ull}, rnv[2] = {0ull, 0ull}, imv[2] = {0ull, 0ull};
-            for (int sb = s0 + grp; sb < s1; sb += 4) {
+            const int s0 = row_ok ? rps[i - row0] : 0, s1 = row_ok ? rps[i - row0 + 1] : 0;
+            const int64_t e0 = (int64_t)(r0 + q0) * a.ldy + 4 * (int64_t)i + p0;
+            const int64_t e1 = e0 + a.ldy;
+            float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;  // in flight during the row
+            if (a.b && row_ok && st0) b0 = *reinterpret_cast<const float4*>(a.b + e0);
+            if (a.b && row_ok && st1) b1 = *reinterpret_cast<const float4*>(a.b + e1);
+            // per right-hand side u (q0) and v (q0 + 1), each over the row pair:
+            // sum re(m) re(x), sum im(m) im(x), sum of the imaginary part
+            unsigned long long rpu = 0ull, rnu = 0ull, imu = 0ull, rpv = 0ull, rnv = 0ull, imv = 0ull;
+            for (int sb = s0 + hh; sb < s1; sb += 2) {  // the two half-warps take alternate blocks
                 const uint32_t lc = lcs[sb];
-                const ulonglong2* m = reinterpret_cast<const ulonglong2*>(st + (uint32_t)sb * 128u);
+                const ulonglong2* m = reinterpret_cast<const ulonglong2*>(mb + (uint32_t)sb * 128u);
                 const float4* u = reinterpret_cast<const float4*>(x0 + lc * 32u);
                 const float4* v = reinterpret_cast<const float4*>(x1 + lc * 32u);
                 const float4 ua = u[0], ub = u[1], va = v[0], vb = v[1];
@@ -247,51 +244,44 @@ __global__ void __launch_bounds__(STG_THREADS, 1) k_spmm_pipe(const PipeArgs a) 
                 const float xv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
+                    const ulonglong2 mc = m[cc];  // (re row p0, re row p0 + 1), (im, im) of column cc
                     const unsigned long long ur = f2pack(xu[2 * cc], xu[2 * cc]), ui = f2pack(xu[2 * cc + 1], xu[2 * cc + 1]);
                     const unsigned long long vr = f2pack(xv[2 * cc], xv[2 * cc]), vi = f2pack(xv[2 * cc + 1], xv[2 * cc + 1]);
-#pragma unroll
-                    for (int P = 0; P < 2; ++P) {
-                        const ulonglong2 mc = m[4 * P + cc];  // (re rows 2P, 2P + 1), (im, im) of column cc
-                        rpu[P] = ffma2(mc.x, ur, rpu[P]);
-                        rnu[P] = ffma2(mc.y, ui, rnu[P]);
-                        imu[P] = ffma2(mc.x, ui, imu[P]);
-                        imu[P] = ffma2(mc.y, ur, imu[P]);
-                        rpv[P] = ffma2(mc.x, vr, rpv[P]);
-                        rnv[P] = ffma2(mc.y, vi, rnv[P]);
-                        imv[P] = ffma2(mc.x, vi, imv[P]);
-                        imv[P] = ffma2(mc.y, vr, imv[P]);
-                    }
+                    rpu = ffma2(mc.x, ur, rpu);
+                    rnu = ffma2(mc.y, ui, rnu);
+                    imu = ffma2(mc.x, ui, imu);
+                    imu = ffma2(mc.y, ur, imu);
+                    rpv = ffma2(mc.x, vr, rpv);
+                    rnv = ffma2(mc.y, vi, rnv);
+                    imv = ffma2(mc.x, vi, imv);
+                    imv = ffma2(mc.y, vr, imv);
                 }
             }
-            float o[16];  // [rhs u, v][row pair P]: (re, im) of rows 2P, 2P + 1
-#pragma unroll
-            for (int P = 0; P < 2; ++P) {
+            float o[8];  // (re, im) of rows p0, p0 + 1 for u, then for v
+            {
                 float a0, a1, n0, n1, i0, i1;
-                f2unpack(rpu[P], a0, a1);
-                f2unpack(rnu[P], n0, n1);
-                f2unpack(imu[P], i0, i1);
-                o[4 * P] = a0 - n0, o[4 * P + 1] = i0, o[4 * P + 2] = a1 - n1, o[4 * P + 3] = i1;
-                f2unpack(rpv[P], a0, a1);
-                f2unpack(rnv[P], n0, n1);
-                f2unpack(imv[P], i0, i1);
-                o[8 + 4 * P] = a0 - n0, o[8 + 4 * P + 1] = i0, o[8 + 4 * P + 2] = a1 - n1, o[8 + 4 * P + 3] = i1;
+                f2unpack(rpu, a0, a1);
+                f2unpack(rnu, n0, n1);
+                f2unpack(imu, i0, i1);
+                o[0] = a0 - n0, o[1] = i0, o[2] = a1 - n1, o[3] = i1;
+                f2unpack(rpv, a0, a1);
+                f2unpack(rnv, n0, n1);
+                f2unpack(imv, i0, i1);
+                o[4] = a0 - n0, o[5] = i0, o[6] = a1 - n1, o[7] = i1;
             }
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {  // the four groups of the row
-                o[e] += __shfl_xor_sync(0xffffffffu, o[e], 4);
-                o[e] += __shfl_xor_sync(0xffffffffu, o[e], 8);
+            for (int e = 0; e < 8; ++e) o[e] += __shfl_xor_sync(0xffffffffu, o[e], 16);  // the other half-warp
+            if (!row_ok || hh) continue;
+            if (st0) {
+                float4 r = make_float4(o[0], o[1], o[2], o[3]);
+                if (a.b) r = make_float4(b0.x - r.x, b0.y - r.y, b0.z - r.z, b0.w - r.w);
+                *reinterpret_cast<float4*>(a.y + e0) = r;
             }
-            if (!row_ok || !sto) continue;
-            // this lane's piece: rhs qo = q0 + (grp >> 1), rows po, po + 1 (po = 2 (grp & 1))
-            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int t = 0; t < 4; ++t)  // constant indices keep o in registers
-                if (t == grp) {
-                    const int e = 8 * (t >> 1) + 4 * (t & 1);
-                    r = make_float4(o[e], o[e + 1], o[e + 2], o[e + 3]);
-                }
-            if (a.b) r = make_float4(bo.x - r.x, bo.y - r.y, bo.z - r.z, bo.w - r.w);
-            *reinterpret_cast<float4*>(a.y + eo) = r;
+            if (st1) {
+                float4 r = make_float4(o[4], o[5], o[6], o[7]);
+                if (a.b) r = make_float4(b1.x - r.x, b1.y - r.y, b1.z - r.z, b1.w - r.w);
+                *reinterpret_cast<float4*>(a.y + e1) = r;
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -349,12 +339,24 @@ void staged_plan_build(cudaStream_t st, StagedPlan& P, const std::vector<int32_t
             ++e;
         }
         if (e == i) return;  // one row alone exceeds the block limit: no plan
+        // shorten the tile until its column list fits the producers and the plan's stage
+        // (the largest blocks, metadata and list over its tiles) still fits twice in shared
+        // memory (rows with many blocks spread over many columns, as on coarse levels)
+        auto meta_bytes = [&](int64_t e_) {
+            return (int)((16 + (size_t)(e_ - i + 1) * 4 + (size_t)(rp[e_] - rp[i]) * 2 + 15) / 16 * 16);
+        };
+        auto fits = [&](int64_t e_, int nc_) {
+            if (nc_ > MAX_TILE_COLS) return false;
+            const StageLayout L = stage_layout(std::max<int>(P.max_blocks, rp[e_] - rp[i]),
+                                               std::max<int>(P.max_meta, meta_bytes(e_)), std::max<int>(P.max_cols, nc_));
+            return L.stages >= 2;
+        };
         int nc = cover(col, rp[i], rp[e], cols, list);
-        while (nc > MAX_TILE_COLS && e > i + 1) {  // shorten the tile until its list fits
+        while (!fits(e, nc) && e > i + 1) {
             --e;
             nc = cover(col, rp[i], rp[e], cols, list);
         }
-        if (nc > MAX_TILE_COLS) return;
+        if (!fits(e, nc)) return;
         blocks = rp[e] - rp[i];
         for (int u = 0; u < nc; ++u) loc[list[u]] = u;
         // metadata record: first and end row (int32, then 2 pad words), row offsets (int32),

@@ -175,7 +175,7 @@ def test_spmv_f32_staged_many_tiles(ect):
     ctx.close()
 
 
-def _oracle_amg(p, M, which):
+def _oracle_amg(p, M, which, blocks=None):
     t = fem.scaling(M)
     S = fem.scaled(M, t)
     s, _ = fem.effective_coefficients(p.sigma, p.nu, p.sigma_d, p.nu_d, which)
@@ -183,7 +183,64 @@ def _oracle_amg(p, M, which):
     d, v = fem.fixed_dofs(p.mesh.bc_mask, cond)
     w = solve.near_null_weights(t, np.concatenate([d, v]))
     G = solve.node_graph_from_tets(p.mesh.n_nodes, p.mesh.tets)
-    return solve.amg_setup(S, w, p.mesh.block_of_node, G)
+    return solve.amg_setup(S, w, p.mesh.block_of_node if blocks is None else blocks, G)
+
+
+def split_blocks(block_of_node, parts):
+    """The smoothing blocks of ect_set_block_split(parts): each subdomain (a contiguous node range)
+    cut into min(parts, n) contiguous pieces at n q / parts."""
+    b = np.asarray(block_of_node)
+    starts = np.flatnonzero(np.r_[True, b[1:] != b[:-1]])
+    ends = np.r_[starts[1:], b.size]
+    out = np.empty(b.size, dtype=np.int64)
+    nb = 0
+    for s0, e0 in zip(starts, ends):
+        n = e0 - s0
+        m = min(parts, n)
+        for q in range(m):
+            out[s0 + n * q // m:s0 + n * (q + 1) // m] = nb
+            nb += 1
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("parts", [2, 4])
+def test_precond_apply_split_blocks(ect, prec, parts):
+    """Block-Jacobi over subdomains cut into 2 or 4 smoothing blocks (the FP32 apply then packs
+    several blocks into each CTA) against the oracle's block-Jacobi over the same blocks, and one
+    W-cycle whose first aggregates are those blocks against the oracle's."""
+    p = E.wall_loss_problem((17, 16, 21), (20e-3, 20e-3, 30e-3), (2, 2, 4), 0.15, 4, z_pos=(0.0,))
+    blocks = split_blocks(p.mesh.block_of_node, parts)
+    M = fem.system_matrix(p, "defect")
+    S = fem.scaled(M, fem.scaling(M))
+    rng = np.random.default_rng(5)
+    n = 4 * p.mesh.n_nodes
+    k = 11                                       # one full tile of 8 and a partial one
+    R = crand(rng, k, n)
+    dt, pr = (torch.complex128, ect.ECT_F64) if prec == "f64" else (torch.complex64, ect.ECT_F32)
+    r = dev(R, dt)
+    mask = ect.ECT_F64 | ect.ECT_F32
+    for group, tol in ((0, 1e-9 if prec == "f64" else 1e-3), (-1, 1e-7 if prec == "f64" else 1e-2)):
+        ctx = ect.Context()
+        ctx.load_problem(p)
+        ctx.set_block_split(parts)
+        ctx.assemble(ect.ECT_DEFECT, mask)
+        ctx.precond_setup(ect.ECT_DEFECT, mask, group)
+        z = torch.empty_like(r)
+        ctx.precond_apply(ect.ECT_DEFECT, r, z, k, precision=pr)
+        Z = z.cpu().numpy()
+        if group == 0:
+            P = solve.block_jacobi(S, blocks)
+            for q in range(k):
+                ref = solve.two_level_apply(P, None, R[q])
+                assert np.linalg.norm(Z[q] - ref) <= tol * np.linalg.norm(ref), (group, q)
+        else:
+            lv = _oracle_amg(p, M, "defect", blocks)
+            for q in range(k):
+                ref = solve.amg_apply(lv, R[q])
+                es = np.linalg.norm(S @ (Z[q] - ref)) / np.linalg.norm(S @ ref)
+                assert es <= tol, (group, q, es)
+        ctx.close()
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])

@@ -297,9 +297,11 @@ int ect_delta_z(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_
  * 64 positions (n_pos > 64 returns ECT_ERR_ARG); every GPU that loads the
  * library keeps it until the process exits.  The first call on a device looks
  * up the array's device address (with that device current) and keeps it for
- * the life of the process.  cudaDeviceReset invalidates the kept address: do not call this function
- * on a device after resetting it.  All calls share the array: calls that
- * overlap on the GPU race.  Synchronises the context stream. */
+ * the life of the process; make that first call on each device before any
+ * stream capture begins.  cudaDeviceReset invalidates the kept address: do
+ * not call this function on a device after resetting it.  All calls share
+ * the array: calls that overlap on the GPU race.  Synchronises the context
+ * stream. */
 int ect_delta_z_static(ect_ctx* ctx, const void* d_u0, const void* d_ud, const void* d_b, const double* h_current,
                        int n_pos, double* h_dz, double* h_dz_emf);
 

@@ -371,134 +371,6 @@ __global__ void __launch_bounds__(64) k_block_apply_sym8x2(const int32_t* __rest
         }
 }
 
-// k_block_apply_sym8x2 with two rows per thread: thread t of a block takes rows
-// t and t + tpb (tpb = threads per block, a power of two >= half the largest
-// block), so each broadcast load of the right-hand-side tile feeds both rows'
-// paired FMAs; 64 / tpb blocks share a CTA.  Dynamic shared memory: per block
-// smax float4 of packed inverse, then the planar tile of 2 tpb rows (real,
-// imaginary parts of the 8 right-hand sides).
-__global__ void __launch_bounds__(64) k_block_apply_sym8r2(const int32_t* __restrict__ block_ptr,
-                                                          const int64_t* __restrict__ poff,
-                                                          const float2* __restrict__ pinv, const float2* __restrict__ r,
-                                                          float2* __restrict__ z, int k, int64_t ld,
-                                                          const int* __restrict__ active,
-                                                          const int32_t* __restrict__ blk_c,
-                                                          const float2* __restrict__ zc, int64_t nc,
-                                                          const float* __restrict__ zv, int accumulate, int ntile,
-                                                          int64_t n_blocks, int tpb_log2, int smax) {
-    constexpr int KT = 8;
-    extern __shared__ __align__(16) float4 dsm[];
-    const int tpb = 1 << tpb_log2, bpc = 64 >> tpb_log2;
-    const int sub = threadIdx.x >> tpb_log2, t = threadIdx.x & (tpb - 1);
-    const int64_t blk = (int64_t)(blockIdx.x / ntile) * bpc + sub;
-    const bool valid = blk < n_blocks;
-    const int r0 = (int)(blockIdx.x % ntile) * KT;
-    const int n0 = valid ? block_ptr[blk] : 0, n1 = valid ? block_ptr[blk + 1] : 0;
-    const int b = 4 * (n1 - n0);
-    const int64_t base = 4 * (int64_t)n0;
-    const int n4 = b * (b + 1) / 4;
-    unsigned onm = 0;
-#pragma unroll
-    for (int q = 0; q < KT; ++q) onm |= ((r0 + q < k) && (!active || active[r0 + q])) ? 1u << q : 0u;
-    if (!onm) return;  // the whole tile has retired (uniform over the CTA, before any barrier)
-    float4* S4s = dsm + (size_t)sub * smax;
-    float* tiles = reinterpret_cast<float*>(dsm + (size_t)bpc * smax);
-    float* rre_s = tiles + (size_t)sub * (2 * tpb) * KT;           // [2 tpb][KT]
-    float* rim_s = tiles + (size_t)(bpc + sub) * (2 * tpb) * KT;   // [2 tpb][KT]
-    if (valid) {
-        const float4* P4 = reinterpret_cast<const float4*>(pinv + poff[blk]);
-        for (int e = t; e < n4; e += tpb) S4s[e] = __ldg(P4 + e);
-    }
-    for (int f = t; f < 2 * tpb * KT; f += tpb) {
-        const int row = f / KT, q = f - row * KT;
-        float2 v = make_float2(0.f, 0.f);
-        if (row < b && ((onm >> q) & 1u)) v = r[(int64_t)(r0 + q) * ld + base + row];
-        rre_s[f] = v.x;
-        rim_s[f] = v.y;
-    }
-    __syncthreads();
-    if (!valid || t >= b) return;
-    const int i0 = t, i1 = t + tpb;
-    const bool has1 = i1 < b;
-    const float2* S = reinterpret_cast<const float2*>(S4s);
-    unsigned long long are0[4], aim0[4], are1[4], aim1[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) are0[h] = aim0[h] = are1[h] = aim1[h] = 0ull;
-    const int ti0 = i0 * (i0 + 1) / 2, ti1 = i1 * (i1 + 1) / 2;
-    int tj = 0;  // j (j + 1) / 2
-#pragma unroll 2
-    for (int j = 0; j < b; ++j) {
-        const float2 a0 = S[j >= i0 ? tj + i0 : ti0 + j];
-        const float2 a1 = has1 ? S[j >= i1 ? tj + i1 : ti1 + j] : make_float2(0.f, 0.f);
-        const ulonglong2 re01 = *reinterpret_cast<const ulonglong2*>(rre_s + j * KT);
-        const ulonglong2 re23 = *reinterpret_cast<const ulonglong2*>(rre_s + j * KT + 4);
-        const ulonglong2 im01 = *reinterpret_cast<const ulonglong2*>(rim_s + j * KT);
-        const ulonglong2 im23 = *reinterpret_cast<const ulonglong2*>(rim_s + j * KT + 4);
-        const unsigned long long vr[4] = {re01.x, re01.y, re23.x, re23.y};
-        const unsigned long long vi[4] = {im01.x, im01.y, im23.x, im23.y};
-        const unsigned long long ax0 = f2pack(a0.x, a0.x), ay0 = f2pack(a0.y, a0.y), nay0 = f2pack(-a0.y, -a0.y);
-        const unsigned long long ax1 = f2pack(a1.x, a1.x), ay1 = f2pack(a1.y, a1.y), nay1 = f2pack(-a1.y, -a1.y);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            are0[h] = ffma2(ax0, vr[h], are0[h]);
-            are0[h] = ffma2(nay0, vi[h], are0[h]);
-            aim0[h] = ffma2(ax0, vi[h], aim0[h]);
-            aim0[h] = ffma2(ay0, vr[h], aim0[h]);
-            are1[h] = ffma2(ax1, vr[h], are1[h]);
-            are1[h] = ffma2(nay1, vi[h], are1[h]);
-            aim1[h] = ffma2(ax1, vi[h], aim1[h]);
-            aim1[h] = ffma2(ay1, vr[h], aim1[h]);
-        }
-        tj += j + 1;
-    }
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        const int i = rr ? i1 : i0;
-        if (rr && !has1) break;
-        float2 acc[KT];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            f2unpack(rr ? are1[h] : are0[h], acc[2 * h].x, acc[2 * h + 1].x);
-            f2unpack(rr ? aim1[h] : aim0[h], acc[2 * h].y, acc[2 * h + 1].y);
-        }
-        if (zc && (i & 3) == 3) {
-            const int cc = blk_c[blk];
-            const float w = zv[n0 + (i >> 2)];
-            if (cc >= 0 && w != 0.f)
-#pragma unroll
-                for (int q = 0; q < KT; ++q) {
-                    if (!((onm >> q) & 1u)) continue;
-                    const float2 v = zc[(int64_t)(r0 + q) * nc + cc];
-                    acc[q].x += w * v.x;
-                    acc[q].y += w * v.y;
-                }
-        }
-#pragma unroll
-        for (int q = 0; q < KT; ++q)
-            if ((onm >> q) & 1u) {
-                float2* zp = z + (int64_t)(r0 + q) * ld + base + i;
-                *zp = accumulate ? cadd(*zp, acc[q]) : acc[q];
-            }
-    }
-}
-
-// launch shape of k_block_apply_sym8r2 for blocks of at most 4 max_block_nodes rows
-struct Sym8r2Shape {
-    int tpb_log2, bpc, smax;
-    size_t smem;
-};
-inline Sym8r2Shape sym8r2_shape(int max_block_nodes) {
-    const int bmax = 4 * max_block_nodes;
-    int lg = 2;  // at least 4 threads per block
-    while ((1 << lg) < (bmax + 1) / 2) ++lg;
-    Sym8r2Shape sh;
-    sh.tpb_log2 = lg;
-    sh.bpc = 64 >> lg;
-    sh.smax = (int)((sym_packed_size(bmax) + 1) / 2);  // float4 per block
-    sh.smem = (size_t)sh.bpc * sh.smax * 16 + (size_t)2 * sh.bpc * (2 << lg) * 8 * sizeof(float);
-    return sh;
-}
-
 // blocks per 64-thread CTA of k_block_apply_sym8x2: as many as fit one thread per row
 inline int sym8_blocks_per_cta(int max_block_nodes) {
     const int b = 4 * max_block_nodes;
@@ -672,11 +544,11 @@ void apply_impl(ect_ctx* c, Matrix& M, const C<T>* pinv, const C<T>* einv, const
     }
     const int32_t* bc = M.blk_c.as<int32_t>();
     if constexpr (std::is_same<T, float>::value) {
-        const Sym8r2Shape sh = sym8r2_shape(c->max_block_nodes);
-        const unsigned grid8 = tile_grid((unsigned)((c->n_blocks + sh.bpc - 1) / sh.bpc), nt);
+        const int bpc = sym8_blocks_per_cta(c->max_block_nodes);
+        const unsigned grid8 = tile_grid((unsigned)((c->n_blocks + bpc - 1) / bpc), nt);
         switch (kt) {
-            case 8: k_block_apply_sym8r2<<<grid8, 64, sh.smem, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv,
-                                                                      0, nt, c->n_blocks, sh.tpb_log2, sh.smax); break;
+            case 8: k_block_apply_sym8x2<<<grid8, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt,
+                                                                c->n_blocks, bpc); break;
             case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
             case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
             default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bp, po, pinv, r, z, k, ld, active, bc, zc, nc, zv, 0, nt); break;
@@ -808,12 +680,11 @@ void block_apply(cudaStream_t st, const int32_t* bptr, const int64_t* poff, cons
     const unsigned grid = tile_grid((unsigned)n_blocks, nt);
     const int acc = accumulate ? 1 : 0;
     if constexpr (std::is_same<T, float>::value) {
-        const Sym8r2Shape sh = sym8r2_shape(max_block_nodes);
-        const unsigned grid8 = tile_grid((unsigned)((n_blocks + sh.bpc - 1) / sh.bpc), nt);
+        const int bpc = sym8_blocks_per_cta(max_block_nodes);
+        const unsigned grid8 = tile_grid((unsigned)((n_blocks + bpc - 1) / bpc), nt);
         switch (kt) {
-            case 8: k_block_apply_sym8r2<<<grid8, 64, sh.smem, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr,
-                                                                      nullptr, 0, nullptr, acc, nt, n_blocks, sh.tpb_log2,
-                                                                      sh.smax); break;
+            case 8: k_block_apply_sym8x2<<<grid8, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0,
+                                                                nullptr, acc, nt, n_blocks, bpc); break;
             case 4: k_block_apply_sym<4><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
             case 2: k_block_apply_sym<2><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;
             default: k_block_apply_sym<1><<<grid, 64, 0, st>>>(bptr, poff, pinv, r, z, k, ld, active, nullptr, nullptr, 0, nullptr, acc, nt); break;

@@ -1,5 +1,5 @@
-"""Delta Z against the oracle at scale (the benchmark spec's 1e-6 bar beyond the
-8k-node parity configuration).
+"""Delta Z against the oracle at scale: the 1e-6 relative bar on Delta Z, checked
+beyond the 8k-node parity configuration.
 
 Expected values come from tests/golden/make_golden.py (CPU oracle only):
   * tsp_mid: a 53 x 53 x 120-node jittered support-plate mesh (337,080 nodes,

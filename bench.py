@@ -502,7 +502,7 @@ def run_reference(args):
     sample = (f"per step: {statistics.median([it for it, _ in v])} oracle FGMRES(30) iterations (multigrid W-cycle) "
               f"on a {'x'.join(map(str, o['shape']))}-node slab of the workload ({o['n_small']} unknowns), "
               f"{ms / 1000:.1f} s; value extrapolated to {o['n_full']} unknowns and {args.ref_iters} iterations "
-              f"per solve (the FP64 count at this size on a GB300); setup {o['setup_s']:.1f} s")
+              f"per solve (the FP64 count at this size on a GB300, bench line fp64_plain); setup {o['setup_s']:.1f} s")
     rec = {"impl": "reference", "metric": "probe solves/s at 4M complex DOF, FP64 plain vs mixed+batched, "
            "dZ err<=1e-6", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "ms_per_step_basis": "measured wall time of one oracle sample",
@@ -670,7 +670,9 @@ def main():
     ap.add_argument("--superlu-limit", type=float, default=60.0,
                     help="seconds allowed for the SuperLU attempt at 64,000 unknowns (0: skip the SuperLU leg)")
     ap.add_argument("--ref-budget", type=float, default=10.0)
-    ap.add_argument("--ref-iters", type=int, default=1410)
+    ap.add_argument("--ref-iters", type=int, default=504,
+                    help="FP64 FGMRES(30) iterations per solve at this size (the GPU's FP64 leg with the "
+                         "autotuned preconditioner), used to extrapolate the reference arm's samples")
     args = ap.parse_args()
     if args.kernel_probe:
         kernel_probe(args)
